@@ -1,0 +1,350 @@
+"""Benchmark of the Tucker-ALS coding path on GB300.
+
+One step = the whole path on one 1920x1080, 2-view x 5-exposure stack
+(paper dims 1920 x 1080 x 3 x 10, IPT, ranks (384, 256, 3, 10), 20 sweeps):
+colour pre-pass of the resident 8-bit images, Tucker-ALS / HOOI, core
+quantiser (16 bits) and reconstruction with the fused residual.  The metric
+is stacks per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank decomposes its own stacks
+(independent problems, weak scaling, no collective on the data path); the
+value is all stacks over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fhd_1920x1080"
+METRIC = "Tucker-ALS stacks/s (1080p, 2x5 exp)"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(sample_sweeps: int = 1):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample
+    of the workload: colour pre-pass, T-HOSVD initialisation and
+    `sample_sweeps` HOOI sweeps of one stack, plus the quantiser, timed and
+    scaled to the full 20-sweep decomposition."""
+    import numpy as np
+    import synth
+    from oracle import colour, quant, tucker
+    cfg = synth.config_spec(WORKLOAD)
+    spec = cfg["spec"]
+    img = synth.make_stack(spec, synth.seed_for(WORKLOAD))
+    t0 = time.perf_counter()
+    T = colour.colour_convert(img, cfg["space"])
+    t1 = time.perf_counter()
+    U = tucker.thosvd(T, cfg["ranks"])
+    t2 = time.perf_counter()
+    res = tucker.hooi(T, cfg["ranks"], sample_sweeps, 0.0, init_factors=U)
+    t3 = time.perf_counter()
+    quant.quantize_planes(quant.planes_of(res.core.astype(np.float32)), 16)
+    t4 = time.perf_counter()
+    per_stack = (t1 - t0) + (t2 - t1) + (t3 - t2) * cfg["iters"] / sample_sweeps + (t4 - t3)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": 1.0 / per_stack, "unit": "stacks/s", "cores": int(cores), "kind": "oracle",
+            "sample": (f"1 stack {spec.s1}x{spec.s2}x3x{spec.K}: colour + T-HOSVD + {sample_sweeps} "
+                       f"HOOI sweep(s) + quantiser, sweep time scaled to {cfg['iters']} sweeps"),
+            "seconds": t4 - t0}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    times = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(1)
+        times.append(1.0 / last["value"])
+    per = statistics.mean(times)
+    val = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "stacks/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": [1920, 1080, 3, 10], "ranks": [384, 256, 3, 10],
+                       "sweeps": 20, "colour": "ipt"},
+            "cpu_baseline": {"value": val, "unit": "stacks/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": val, "unit": "stacks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mes", choices=["mes", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2104_04726_gb300 as mes
+    import synth
+    from paper_2104_04726_gb300 import _lib
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if dist is not None:
+        dist.barrier()
+    lib = _lib.load()
+
+    name = args.workload
+    cfg = synth.config_spec(name)
+    spec = cfg["spec"]
+    dims = [spec.s1, spec.s2, 3, spec.K]
+    ranks = list(cfg["ranks"])
+    iters = cfg["iters"]
+    img = synth.make_stack(spec, synth.seed_for(name, rank))
+    rgb_host = torch.from_numpy(img).pin_memory()
+    rgb = rgb_host.to(dev)
+
+    # device-resident outputs reused by every step
+    X = torch.empty(torch.Size([spec.K, 3, spec.s2, spec.s1]), dtype=torch.float32, device=dev)
+    n2 = torch.empty((), dtype=torch.float64, device=dev)
+    core = torch.empty(mes.torch_shape(ranks), dtype=torch.float32, device=dev)
+    facs = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
+    fit = torch.empty((), dtype=torch.float64, device=dev)
+    itd = torch.zeros((), dtype=torch.int32, device=dev)
+    outs = (core, facs, fit, itd, None)
+
+    def step():
+        mes.colour_convert(rgb, cfg["space"], out=X, norm2=n2)
+        mes.tucker_als(X, dims, ranks, max_iters=iters, tol=0.0, precision=args.precision, outputs=outs)
+        q, sc = mes.quantize_core(core, ranks, 16)
+        Xh, sse = mes.reconstruct(core, facs, dims, ranks, ref=X)
+        return q, sc, sse
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device events, barrier + sync on both sides
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    stacks = args.steps * world
+    value = stacks / (ms_max / 1e3)
+
+    # ---- per-kernel profile over the same K steps (events on the launch stream)
+    lib.mes_profile_enable(1)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    fams = []
+    for i in range(lib.mes_profile_count()):
+        nm = ctypes.create_string_buffer(64)
+        n = ctypes.c_int64()
+        t_ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _lib.check(lib.mes_profile_get(i, nm, 64, ctypes.byref(n), ctypes.byref(t_ms), ctypes.byref(fl),
+                                       ctypes.byref(by)), "mes_profile_get")
+        fams.append({"name": nm.value.decode(), "launches": n.value, "ms": t_ms.value, "flops": fl.value,
+                     "bytes": by.value})
+    lib.mes_profile_enable(0)
+    fams.sort(key=lambda f: -f["ms"])
+    total_ms = sum(f["ms"] for f in fams) or 1.0
+    launches = sum(f["launches"] for f in fams) // max(args.steps, 1) * args.steps
+
+    peaks, peak_src = _peaks()
+    top = fams[0]
+    if top["name"].startswith("gemm_f32") or top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
+        # FP32 CUDA-core GEMM: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz')} MHz",
+                "share": top["ms"] / total_ms}
+    else:
+        achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "share": top["ms"] / total_ms}
+
+    # ---- end to end through the public API with host buffers
+    q_host = torch.empty(mes.torch_shape(ranks), dtype=torch.int16, pin_memory=True)
+    P = 1
+    for r in ranks[2:]:
+        P *= r
+    s_host = torch.empty((P,), dtype=torch.float32, pin_memory=True)
+    f_host = [torch.empty((r, s), dtype=torch.float32, pin_memory=True) for s, r in zip(dims, ranks)]
+    fit_host = torch.empty((), dtype=torch.float64, pin_memory=True)
+    h2d = rgb_host.numel()
+    d2h = q_host.numel() * 2 + P * 4 + sum(f.numel() * 4 for f in f_host) + 8
+
+    def e2e_step():
+        rgb.copy_(rgb_host, non_blocking=True)
+        q, sc, _ = step()
+        q_host.copy_(q, non_blocking=True)
+        s_host.copy_(sc, non_blocking=True)
+        for a, b in zip(f_host, facs):
+            a.copy_(b, non_blocking=True)
+        fit_host.copy_(fit, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e2 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    e2[0].record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e2[1].record(stream)
+    torch.cuda.synchronize()
+    t2 = torch.tensor([e2[0].elapsed_time(e2[1])], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_val = stacks / (float(t2.item()) / 1e3)
+
+    fit_val = float(fit.item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "stacks/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+                "data": "synthetic",
+                "config": {"workload": name, "dims": dims, "ranks": ranks, "sweeps": iters, "colour": cfg["space"],
+                           "precision": args.precision, "quant_bits": 16,
+                           "l2": "inputs larger than L2 (stack 249 MB FP32 + second layout 249 MB per step)",
+                           "parallelism": f"stack-parallel x{world}"},
+                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+                "e2e": {"value": e2e_val, "unit": "stacks/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "fit": fit_val,
+                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in f.items()} for f in fams[:8]]}
+        if not args.no_cpu_baseline and world == 1:
+            cb = cpu_baseline(1)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * mes.h -- C ABI of the GB300 (sm_103a) library for the Tucker-ALS stage of
+ * multi-exposure stereo coding (Sharma & Grover, arXiv 2104.04726).
+ *
+ * The library covers the data-parallel path of the coding scheme:
+ *   colour pre-pass (Section III-A)  ->  Tucker-ALS / HOOI decomposition of
+ *   the stacked tensor (Section III-B, Eq. 1 to Eq. 8)  ->  core quantiser
+ *   and reconstruction.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns mes_status.  No C++ exception crosses the ABI.  On an
+ *    error, mes_last_error() returns a thread-local message.
+ *  - Array arguments are DEVICE pointers owned by the caller unless a
+ *    parameter says otherwise.  The library never frees them.
+ *  - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t
+ *    passed as void*; NULL is the legacy default stream) and the call returns
+ *    without synchronising, except where a parameter says so.  Scalar results
+ *    (fit, iteration count, norms) are written to device memory so calls stay
+ *    asynchronous.
+ *  - Tensors are dense with the FIRST mode fastest: element (i_1, ..., i_N)
+ *    of a tensor of dims (s_1, ..., s_N) is at
+ *    i_1 + s_1 * (i_2 + s_2 * (i_3 + ...)).
+ *    Factor matrices are column-major s_n x r_n (element (i, q) at i + s_n*q).
+ *  - Internal scratch memory is taken from the stream-ordered allocator
+ *    (cudaMallocAsync on `stream`) and released on the same stream before
+ *    the call returns.  MES_ERR_OOM reports a failed allocation.
+ *  - Invalid arguments are rejected before anything is enqueued.
+ */
+#ifndef MES_H
+#define MES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mes_status {
+  MES_OK = 0,
+  MES_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum            */
+  MES_ERR_RANK = 2,          /* r_n < 1, r_n > s_n, or r_n > prod_{m!=n} r_m */
+  MES_ERR_OOM = 3,           /* device allocation failed                    */
+  MES_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed        */
+  MES_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up          */
+  MES_ERR_NONFINITE = 6,     /* NaN or Inf met where the method forbids it  */
+  MES_ERR_NOT_IMPLEMENTED = 7
+} mes_status;
+
+typedef enum mes_colour {
+  MES_YCBCR601 = 0,   /* ITU-R BT.601 Y'CbCr, full range, no offsets        */
+  MES_IPT = 1         /* Ebner-Fairchild IPT from gamma-linearised sRGB    */
+} mes_colour;
+
+typedef enum mes_precision {
+  MES_PREC_FP32 = 0,  /* every contraction in FP32 (CUDA cores)            */
+  MES_PREC_BF16 = 1,  /* tensor-core BF16 inputs, FP32 accumulation        */
+  MES_PREC_BF16X3 = 2 /* split-BF16 (hi+lo, three products), FP32 accum.   */
+} mes_precision;
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* mes_last_error(void);
+
+/* Library version string, e.g. "mes 0.1.0 sm_103a". */
+const char* mes_version(void);
+
+/*
+ * mes_colour_convert -- colour pre-pass of Section III-A and the stacking of
+ * Section III-B ("T_MES^c", the tensor of multi-exposure stereo images).
+ *
+ *  rgb8   [in]  K images, each row-major with s1 pixels per row and s2 rows,
+ *               interleaved R,G,B bytes: byte (k, y, x, c) at
+ *               ((k*s2 + y)*s1 + x)*3 + c.  Image k = view*E + exposure.
+ *  s1, s2, K    image width, height and count (each >= 1).
+ *  space        MES_YCBCR601 or MES_IPT.
+ *  gamma        IPT only: linearisation exponent R = (R')^gamma (> 0).
+ *  out    [out] FP32 tensor of dims (s1, s2, 3, K), first mode fastest, i.e.
+ *               channel plane (c, k) is the contiguous s1*s2 block number
+ *               c + 3k.
+ *  norm2  [out] nullable; one double receiving ||out||_F^2 (accumulated in
+ *               FP64 with a fixed reduction order: bitwise reproducible).
+ * Errors: MES_ERR_INVALID_ARG for null rgb8/out, non-positive sizes, an
+ *         unknown space or gamma <= 0; MES_ERR_CUDA on a launch failure.
+ */
+mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K,
+                              int space, float gamma, float* out, double* norm2,
+                              void* stream);
+
+/*
+ * Options of mes_tucker_als.  Zero-initialise and set what you need; a NULL
+ * options pointer means all defaults.  Fields equal to 0 take the default.
+ */
+typedef struct mes_als_opts {
+  int precision;        /* mes_precision of the large contractions (FP32)     */
+  int init_iters;       /* subspace steps of the T-HOSVD initialisation (4)   */
+  int inner_iters;      /* subspace steps per factor update in a sweep (2)    */
+  uint64_t seed;        /* seed of the random start block of the init (1)     */
+  const float* const* init_factors; /* nullable: device factors to start from
+                                       instead of T-HOSVD (warm start / resume) */
+  int* iters_done;      /* nullable device int: sweeps actually run           */
+  double* fit_history;  /* nullable device array of max_iters doubles: fit
+                           after each sweep from ||T||^2 - ||Q||^2            */
+  int canonical;        /* 0 = default (1): rotate each factor to the
+                           eigenvectors of the core's mode-n Gram, sorted by
+                           decreasing eigenvalue, sign-fixed; -1 = off        */
+} mes_als_opts;
+
+/*
+ * mes_tucker_als -- Tucker-ALS / HOOI of Section III-B.
+ *
+ * Computes T ~= Q x_1 S^(1) x_2 ... x_N S^(N) (Eq. 1) with orthonormal
+ * factors S^(n) (s_n x r_n), initialised by the truncated HOSVD (Eq. 6,
+ * Eq. 7) and refined by sweeps n = 1..N in which S^(n) becomes the r_n
+ * leading left singular vectors of Y^(n) = T x_{i!=n} S^(i)T (Eq. 8), i.e.
+ * the leading eigenvectors of the Gram Y^(n)_(n) Y^(n)_(n)^T.
+ *
+ *  X        [in]  FP32 tensor of dims `dims`, first mode fastest.
+ *  N              order, 2..8.  Modes 1 and 2 may have any size; modes 3..N
+ *                 must have s_n <= 32 and prod_{n>=3} s_n <= 1024.
+ *  dims, ranks    HOST arrays of N int64.
+ *  max_iters      maximum number of sweeps (>= 1).
+ *  tol            stop after sweep t > 1 when |fit_t - fit_{t-1}| < tol.
+ *  core     [out] FP32 tensor of dims `ranks`, first mode fastest.
+ *  factors  [in]  HOST array of N DEVICE pointers; factors[n] [out] receives
+ *                 S^(n), column-major s_n x r_n.
+ *  fit      [out] nullable device double: 1 - ||T - T_hat||_F / ||T||_F of the
+ *                 returned decomposition, from the explicit residual.
+ *  opts           nullable, see mes_als_opts.
+ * Errors: MES_ERR_INVALID_ARG (null pointers, N out of range, bad sizes or
+ *         options), MES_ERR_RANK (rank constraints), MES_ERR_OOM,
+ *         MES_ERR_CUDA.
+ */
+mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
+                          int max_iters, double tol, float* core, float* const* factors,
+                          double* fit, const mes_als_opts* opts, void* stream);
+
+/*
+ * mes_reconstruct -- T_hat = Q x_1 S^(1) x_2 ... x_N S^(N) (Eq. 1, Eq. 2).
+ *
+ *  core     [in]  FP32 tensor of dims `ranks`.
+ *  factors  [in]  HOST array of N device pointers, column-major s_n x r_n.
+ *  out      [out] FP32 tensor of dims `dims`.
+ *  ref      [in]  nullable FP32 tensor of dims `dims`; when given, sse
+ *                 receives sum((ref - out)^2) in FP64 (fused into the last
+ *                 contraction; bitwise reproducible).
+ *  sse      [out] nullable device double.
+ * Same shape limits and errors as mes_tucker_als.
+ */
+mes_status mes_reconstruct(const float* core, const float* const* factors, int N,
+                           const int64_t* dims, const int64_t* ranks, float* out,
+                           const float* ref, double* sse, void* stream);
+
+/*
+ * mes_quantize_core -- core quantiser, the rate knob of the scheme (the
+ * abstract and Section I: bitrate set "by changing the rank of core tensor
+ * and its quantization"; the paper does not define the quantiser).
+ *
+ * The core (r_1 x r_2 x r_3 x ... x r_N) is cut into P = prod_{n>=3} r_n
+ * planes of r_1 x r_2 (plane p is the contiguous block p of the first-mode-
+ * fastest core).  Per plane: m = max|x|, qmax = 2^(bits-1) - 1,
+ * scale = m / qmax (one FP32 division), q = clamp(rint(x / scale), -qmax,
+ * qmax) with FP32 division and round-half-to-even; m == 0 gives scale 0 and
+ * q 0.  Results are bit-exact against any IEEE FP32 implementation of the
+ * same steps.
+ *
+ *  core    [in]  FP32, N >= 1 modes (N = 1: one plane of r_1 x 1).
+ *  ranks   HOST array of N int64 (each >= 1).
+ *  bits    2..16.
+ *  q       [out] int16, same element order as the core.
+ *  scales  [out] FP32, P entries.
+ * Errors: MES_ERR_INVALID_ARG; MES_ERR_NONFINITE if a plane holds NaN or
+ *         Inf (reported only when `status_host_sync` != 0, since it needs a
+ *         device-to-host read; otherwise such planes get scale NaN).
+ */
+mes_status mes_quantize_core(const float* core, int N, const int64_t* ranks, int bits,
+                             int16_t* q, float* scales, int status_host_sync, void* stream);
+
+/* Inverse of mes_quantize_core: x = q * scale (FP32), same layouts. */
+mes_status mes_dequantize_core(const int16_t* q, const float* scales, int N,
+                               const int64_t* ranks, float* core, void* stream);
+
+/*
+ * Measurement helpers (the paper has no counterpart: they exist to report
+ * per-kernel time against the roofline).  When enabled, every kernel launch
+ * of the library is bracketed by CUDA events recorded on the launch stream
+ * and its algorithmic flops and bytes are accumulated per kernel family.
+ * Not for use while a stream is being captured into a CUDA graph.
+ *
+ * mes_profile_enable(1) clears the records and starts recording; 0 stops.
+ * mes_profile_count() is the number of kernel families recorded.
+ * mes_profile_get(i, ...) synchronises on family i's events and returns its
+ *   name (NUL-terminated, at most name_len bytes, host buffer), launch count,
+ *   total device milliseconds, flops and bytes (host pointers, nullable).
+ *   MES_ERR_INVALID_ARG for a bad index or buffer, MES_ERR_CUDA if an event
+ *   query fails.
+ */
+void mes_profile_enable(int on);
+int mes_profile_count(void);
+mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, double* ms,
+                           double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MES_H */

@@ -156,3 +156,13 @@ def psnr(T: np.ndarray, T_hat: np.ndarray) -> float:
     if mse == 0.0:
         return float("inf")
     return 10.0 * np.log10(peak * peak / mse)
+
+
+def element(core: np.ndarray, factors, idx) -> float:
+    """One entry of the Tucker model, Eq. 2:
+    T_hat(t_1..t_N) = sum_{q_1..q_N} Q(q_1..q_N) prod_r S^(r)(t_r, q_r)."""
+    out = np.asarray(core, dtype=np.float64)
+    for U, t in zip(factors, idx):
+        # contract the leading mode with row t of its factor
+        out = np.tensordot(np.asarray(U, dtype=np.float64)[t], out, axes=(0, 0))
+    return float(out)

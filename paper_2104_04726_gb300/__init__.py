@@ -1,0 +1,178 @@
+"""GB300 (sm_103a) Tucker-ALS library for multi-exposure stereo coding
+(Sharma & Grover, arXiv 2104.04726, Section III).
+
+Thin Python binding over the C ABI of `include/mes.h`: every function here
+only marshals torch tensors (device memory) and the current CUDA stream into
+the library call; all computation runs in the library's CUDA kernels.
+
+Tensor conventions: the library stores tensors first-mode fastest.  A tensor
+of paper dims (s_1, ..., s_N) is held in a C-contiguous torch tensor of shape
+(s_N, ..., s_1); a factor S^(n) (s_n x r_n, column-major) is a C-contiguous
+torch tensor of shape (r_n, s_n).  `paper_dims(t)` / `torch_shape(dims)`
+convert between the two.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+from . import _lib
+
+__all__ = ["colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequantize_core",
+           "version", "torch_shape", "paper_dims", "PRECISIONS", "SPACES", "MesError"]
+
+MesError = _lib.MesError
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+SPACES = {"ycbcr": 0, "ipt": 1}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def version() -> str:
+    return _lib.load().mes_version().decode()
+
+
+def torch_shape(dims: Sequence[int]) -> tuple:
+    return tuple(int(d) for d in reversed(list(dims)))
+
+
+def paper_dims(t) -> tuple:
+    return tuple(int(d) for d in reversed(list(t.shape)))
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _i64(vals):
+    arr = (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def _need(t, dtype, name):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+
+
+def colour_convert(rgb8, space: str = "ycbcr", gamma: float = 2.2, out=None, norm2=None):
+    """Colour pre-pass (Section III-A).  rgb8: uint8 CUDA tensor (K, s2, s1, 3).
+    Returns (T, norm2): T float32 of torch shape (K, 3, s2, s1) = paper dims
+    (s1, s2, 3, K); norm2 a float64 CUDA scalar tensor with ||T||_F^2."""
+    torch = _torch()
+    _need(rgb8, torch.uint8, "rgb8")
+    K, s2, s1, c = rgb8.shape
+    if c != 3:
+        raise ValueError("rgb8 must have 3 channels")
+    if out is None:
+        out = torch.empty((K, 3, s2, s1), dtype=torch.float32, device=rgb8.device)
+    if norm2 is None:
+        norm2 = torch.empty((), dtype=torch.float64, device=rgb8.device)
+    lib = _lib.load()
+    st = lib.mes_colour_convert(_ptr(rgb8), s1, s2, K, SPACES[space], ctypes.c_float(gamma),
+                                _ptr(out), _ptr(norm2), _stream())
+    _lib.check(st, "mes_colour_convert")
+    return out, norm2
+
+
+def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
+               precision: str = "fp32", init_iters: int = 0, inner_iters: int = 0, seed: int = 0,
+               canonical: bool = True, init_factors=None, history: bool = False, outputs=None):
+    """Tucker-ALS / HOOI (Section III-B).  X: float32 CUDA tensor holding the
+    first-mode-fastest tensor of paper dims `dims`.  Returns a dict with
+    `core` (torch shape reversed(ranks)), `factors` (list of (r_n, s_n)
+    tensors = column-major S^(n)), `fit` (float64 CUDA scalar), `iters`
+    (int32 CUDA scalar) and, if history, `fit_history` (max_iters float64)."""
+    torch = _torch()
+    _need(X, torch.float32, "X")
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    N = len(dims)
+    if len(ranks) != N:
+        raise ValueError("dims and ranks differ in length")
+    n_el = 1
+    for d in dims:
+        n_el *= d
+    if X.numel() != n_el:
+        raise ValueError("X does not hold prod(dims) elements")
+    dev = X.device
+    if outputs is None:
+        core = torch.empty(torch_shape(ranks), dtype=torch.float32, device=dev)
+        factors = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
+        fit = torch.empty((), dtype=torch.float64, device=dev)
+        iters = torch.zeros((), dtype=torch.int32, device=dev)
+        hist = torch.full((max_iters,), float("nan"), dtype=torch.float64, device=dev) if history else None
+    else:
+        core, factors, fit, iters, hist = outputs
+    fac_arr = (ctypes.c_void_p * N)(*[f.data_ptr() for f in factors])
+    opts = _lib.MesAlsOpts()
+    opts.precision = PRECISIONS[precision]
+    opts.init_iters = int(init_iters)
+    opts.inner_iters = int(inner_iters)
+    opts.seed = int(seed)
+    opts.canonical = 0 if canonical else -1
+    opts.iters_done = iters.data_ptr()
+    opts.fit_history = hist.data_ptr() if hist is not None else None
+    keep = None
+    if init_factors is not None:
+        keep = (ctypes.c_void_p * N)(*[f.data_ptr() for f in init_factors])
+        opts.init_factors = ctypes.cast(keep, ctypes.POINTER(ctypes.c_void_p))
+    lib = _lib.load()
+    st = lib.mes_tucker_als(_ptr(X), N, _i64(dims), _i64(ranks), int(max_iters), float(tol), _ptr(core),
+                            fac_arr, _ptr(fit), ctypes.byref(opts), _stream())
+    _lib.check(st, "mes_tucker_als")
+    out = {"core": core, "factors": factors, "fit": fit, "iters": iters}
+    if hist is not None:
+        out["fit_history"] = hist
+    return out
+
+
+def reconstruct(core, factors, dims: Sequence[int], ranks: Sequence[int], out=None, ref=None):
+    """T_hat = Q x_1 S^(1) ... x_N S^(N) (Eq. 1).  With `ref`, also returns
+    sum((ref - T_hat)^2) as a float64 CUDA scalar (fused)."""
+    torch = _torch()
+    _need(core, torch.float32, "core")
+    N = len(dims)
+    if out is None:
+        out = torch.empty(torch_shape(dims), dtype=torch.float32, device=core.device)
+    sse = torch.empty((), dtype=torch.float64, device=core.device) if ref is not None else None
+    fac_arr = (ctypes.c_void_p * N)(*[f.data_ptr() for f in factors])
+    lib = _lib.load()
+    st = lib.mes_reconstruct(_ptr(core), fac_arr, N, _i64(dims), _i64(ranks), _ptr(out), _ptr(ref),
+                             _ptr(sse), _stream())
+    _lib.check(st, "mes_reconstruct")
+    return (out, sse) if ref is not None else out
+
+
+def quantize_core(core, ranks: Sequence[int], bits: int = 16, check_finite: bool = False):
+    """Per-plane quantiser of the core.  Returns (q int16 like core, scales
+    float32 of prod(ranks[2:]) entries)."""
+    torch = _torch()
+    _need(core, torch.float32, "core")
+    P = 1
+    for r in ranks[2:]:
+        P *= int(r)
+    q = torch.empty(core.shape, dtype=torch.int16, device=core.device)
+    scales = torch.empty((P,), dtype=torch.float32, device=core.device)
+    lib = _lib.load()
+    st = lib.mes_quantize_core(_ptr(core), len(ranks), _i64(ranks), int(bits), _ptr(q), _ptr(scales),
+                               1 if check_finite else 0, _stream())
+    _lib.check(st, "mes_quantize_core")
+    return q, scales
+
+
+def dequantize_core(q, scales, ranks: Sequence[int]):
+    torch = _torch()
+    core = torch.empty(q.shape, dtype=torch.float32, device=q.device)
+    lib = _lib.load()
+    st = lib.mes_dequantize_core(_ptr(q), _ptr(scales), len(ranks), _i64(ranks), _ptr(core), _stream())
+    _lib.check(st, "mes_dequantize_core")
+    return core

@@ -1,0 +1,90 @@
+"""ctypes loader of the in-tree CUDA library (`_build/libmes.so`).
+
+Argument marshalling only.  Loading fails loudly when the library has not
+been built: there is no fallback implementation of any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmes.so")
+
+STATUS = {
+    0: "MES_OK",
+    1: "MES_ERR_INVALID_ARG",
+    2: "MES_ERR_RANK",
+    3: "MES_ERR_OOM",
+    4: "MES_ERR_CUDA",
+    5: "MES_ERR_TIMEOUT",
+    6: "MES_ERR_NONFINITE",
+    7: "MES_ERR_NOT_IMPLEMENTED",
+}
+
+# Entry points declared in include/mes.h, with their ctypes signatures.
+_c = ctypes
+_p = _c.c_void_p
+_i64p = _c.POINTER(_c.c_int64)
+SIGNATURES = {
+    "mes_last_error": (_c.c_char_p, []),
+    "mes_version": (_c.c_char_p, []),
+    "mes_colour_convert": (_c.c_int, [_p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _c.c_float,
+                                      _p, _p, _p]),
+    "mes_tucker_als": (_c.c_int, [_p, _c.c_int, _i64p, _i64p, _c.c_int, _c.c_double, _p,
+                                  _c.POINTER(_p), _p, _p, _p]),
+    "mes_reconstruct": (_c.c_int, [_p, _c.POINTER(_p), _c.c_int, _i64p, _i64p, _p, _p, _p, _p]),
+    "mes_quantize_core": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _c.c_int, _p]),
+    "mes_dequantize_core": (_c.c_int, [_p, _p, _c.c_int, _i64p, _p, _p]),
+    "mes_profile_enable": (None, [_c.c_int]),
+    "mes_profile_count": (_c.c_int, []),
+    "mes_profile_get": (_c.c_int, [_c.c_int, _c.c_char_p, _c.c_int, _i64p, _c.POINTER(_c.c_double),
+                                   _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
+}
+
+
+class MesAlsOpts(ctypes.Structure):
+    """Mirror of `mes_als_opts` in include/mes.h."""
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("init_iters", ctypes.c_int),
+        ("inner_iters", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("init_factors", ctypes.POINTER(ctypes.c_void_p)),
+        ("iters_done", ctypes.c_void_p),
+        ("fit_history", ctypes.c_void_p),
+        ("canonical", ctypes.c_int),
+    ]
+
+
+class MesError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name}: {msg}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once) and attach the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library not built ({path} missing); run `python -m paper_2104_04726_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        msg = load().mes_last_error().decode(errors="replace")
+        raise MesError(status, where, msg)

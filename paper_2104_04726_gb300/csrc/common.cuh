@@ -1,0 +1,108 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "mes.h"
+
+namespace mes {
+
+// Records a formatted message in the thread-local error buffer and returns s.
+mes_status fail(mes_status s, const char* fmt, ...);
+void clear_error();
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Host-side bounds audit.  Buffers of known extent (scratch allocations and
+// the caller's arrays whose sizes follow from the call's arguments) are
+// registered for the duration of an ABI call; every launch descriptor is
+// checked against them before the launch, so an addressing mistake returns
+// an error instead of touching memory out of range.
+void audit_register(const void* p, size_t bytes);
+void audit_clear();
+// Returns MES_OK when [p, p + last_byte] lies inside the registered buffer
+// that contains p (or when p is not in any registered buffer).
+mes_status audit(const void* p, size_t last_byte, const char* what);
+
+// Per-kernel-family profiler (off by default).  When on, every launch is
+// bracketed by CUDA events recorded on its own stream, and the algorithmic
+// flops and bytes of the launch are accumulated per family.  Not usable
+// inside stream capture.
+bool prof_on();
+void prof_begin(cudaStream_t st);
+void prof_end(const char* family, cudaStream_t st, double flops, double bytes);
+
+struct ProfScope {
+  const char* fam;
+  cudaStream_t st;
+  double flops, bytes;
+  ProfScope(const char* f, cudaStream_t s, double fl, double by) : fam(f), st(s), flops(fl), bytes(by) {
+    if (prof_on()) prof_begin(st);
+  }
+  ~ProfScope() {
+    if (prof_on()) prof_end(fam, st, flops, bytes);
+  }
+};
+
+struct AuditScope {
+  AuditScope() { audit_clear(); }
+  ~AuditScope() { audit_clear(); }
+};
+
+// Stream-ordered scratch allocation; every allocation of one ABI call is
+// released on the same stream before the call returns.
+struct Scratch {
+  cudaStream_t stream;
+  void* ptrs[64];
+  int n = 0;
+  explicit Scratch(cudaStream_t s) : stream(s) {}
+  ~Scratch() {
+    for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], stream);
+  }
+  template <class T>
+  mes_status alloc(T** out, size_t count) {
+    if (n >= 64) return fail(MES_ERR_OOM, "scratch table full");
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~size_t(255), stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MES_ERR_OOM, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ptrs[n++] = p;
+    audit_register(p, bytes);
+    *out = static_cast<T*>(p);
+    return MES_OK;
+  }
+};
+
+inline unsigned grid_for(int64_t work, int threads, int64_t cap) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return static_cast<unsigned>(b);
+}
+
+}  // namespace mes
+
+#define MES_TRY(expr)                      \
+  do {                                     \
+    mes_status s_ = (expr);                \
+    if (s_ != MES_OK) return s_;           \
+  } while (0)
+
+#define MES_CUDA_TRY(expr)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
+      return mes::fail(MES_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                       __FILE__, __LINE__);                                                 \
+    }                                                                                       \
+  } while (0)
+
+#define MES_LAUNCH_CHECK() MES_CUDA_TRY(cudaGetLastError())

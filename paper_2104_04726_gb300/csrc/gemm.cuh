@@ -1,0 +1,44 @@
+// Descriptor of a batched strided product C(m, n) = alpha * sum_k A(m, k) B(n, k)
+// (+ C(m, n) when accumulate).  Every tensor contraction of the Tucker-ALS
+// sweep is written as one of these, with layouts chosen so that no transpose
+// pass is needed:
+//
+//   A(m, k) at A + m*a_m + k_lo*a_k + k_hi*a_kh + b*a_b,  k = k_lo + K_lo*k_hi
+//   B(n, k) at B + n*b_n + k_lo*b_k + k_hi*b_kh + b*b_b
+//   C(m, n) at C + m_lo*c_m + m_hi*c_mh + n_lo*c_n + n_hi*c_nh + b*c_b,
+//            m = m_lo + M_lo*m_hi,  n = n_lo + N_lo*n_hi
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace mes {
+
+struct Gemm {
+  int64_t M = 0, N = 0, K_lo = 0, K_hi = 1;
+  int batch = 1;
+  const float* A = nullptr;
+  int64_t a_m = 0, a_k = 0, a_kh = 0, a_b = 0;
+  const float* B = nullptr;
+  int64_t b_n = 0, b_k = 0, b_kh = 0, b_b = 0;
+  float* C = nullptr;
+  int64_t M_lo = 0, c_m = 0, c_mh = 0, N_lo = 0, c_n = 0, c_nh = 0, c_b = 0;
+  float alpha = 1.f;
+  bool accumulate = false;
+  const int* skip = nullptr;      // device flag: when non-zero the launch is a no-op
+  // Residual mode: instead of storing, accumulate sum((ref - alpha*AB)^2) in
+  // FP64; ref is addressed like C.  partials needs gemm_partials(g) doubles.
+  const float* ref = nullptr;
+  double* partials = nullptr;
+};
+
+// FP32 CUDA-core path.
+mes_status gemm_f32(const Gemm& g, cudaStream_t st);
+// Number of per-block partial sums the residual mode writes.
+int64_t gemm_partials(const Gemm& g);
+// Sums n doubles in a fixed order into *out (one block).
+mes_status sum_doubles(const double* partials, int64_t n, double* out, const int* skip,
+                       cudaStream_t st);
+
+}  // namespace mes

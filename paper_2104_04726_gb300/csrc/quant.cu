@@ -1,0 +1,157 @@
+// Core quantiser (the rate knob of the scheme: "the rank of core tensor and
+// its quantization", abstract and Section I).  Per r1 x r2 plane of the core:
+// m = max|x| (exact), scale = m / qmax, q = clamp(rint(x / scale)).
+//
+// Two bandwidth passes over the core:
+//   1. per-(plane, chunk) block max of |x| as IEEE bit patterns (for x >= 0
+//      the unsigned order of the bits is the float order, so atomicMax on the
+//      bits is an exact, order-free max), into a per-plane scratch word;
+//   2. quantise every element with IEEE round-to-nearest division
+//      (__fdiv_rn) and round-half-even conversion (__float2int_rn).
+// Built without fast-math, so both divisions are correctly rounded and the
+// codes are bit-exact against any IEEE FP32 implementation of the same steps.
+#include "common.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads)
+plane_absmax_kernel(const float* __restrict__ core, int64_t plane_size, int64_t chunk,
+                    unsigned* __restrict__ maxbits) {
+  const int64_t p = blockIdx.y;
+  const int64_t begin = (int64_t)blockIdx.x * chunk;
+  int64_t end = begin + chunk;
+  if (end > plane_size) end = plane_size;
+  const float* src = core + p * plane_size;
+  unsigned m = 0u;
+  for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+    unsigned b = __float_as_uint(fabsf(__ldg(src + i)));
+    m = max(m, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ unsigned red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0u;
+    for (int w = 0; w < kThreads / 32; ++w) t = max(t, red[w]);
+    atomicMax(maxbits + p, t);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+quantize_kernel(const float* __restrict__ core, int64_t plane_size, int64_t total,
+                const unsigned* __restrict__ maxbits, float qmax, int16_t* __restrict__ q,
+                float* __restrict__ scales) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t p = i / plane_size;
+    const float m = __uint_as_float(maxbits[p]);
+    int16_t code = 0;
+    float scale = 0.f;
+    if (m != 0.f) {
+      scale = __fdiv_rn(m, qmax);
+      float v = __fdiv_rn(core[i], scale);
+      int c = __float2int_rn(v);
+      int iq = (int)qmax;
+      c = c > iq ? iq : (c < -iq ? -iq : c);
+      code = (int16_t)c;
+    }
+    q[i] = code;
+    if (i - p * plane_size == 0) scales[p] = scale;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+dequantize_kernel(const int16_t* __restrict__ q, const float* __restrict__ scales,
+                  int64_t plane_size, int64_t total, float* __restrict__ core) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t p = i / plane_size;
+    core[i] = __fmul_rn((float)q[i], scales[p]);
+  }
+}
+
+mes_status plane_shape(int N, const int64_t* ranks, int64_t* plane_size, int64_t* planes) {
+  if (N < 1 || N > 8 || !ranks) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: N must be 1..8");
+  for (int n = 0; n < N; ++n)
+    if (ranks[n] < 1) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: ranks must be >= 1");
+  *plane_size = ranks[0] * (N >= 2 ? ranks[1] : 1);
+  int64_t P = 1;
+  for (int n = 2; n < N; ++n) P *= ranks[n];
+  *planes = P;
+  if (P > 65535) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: more than 65535 planes");
+  return MES_OK;
+}
+
+}  // namespace
+
+namespace mes {
+
+// Launches both passes; maxbits must hold `planes` words and is cleared here.
+mes_status quantize_launch(const float* core, int64_t plane_size, int64_t planes, int bits,
+                           int16_t* q, float* scales, unsigned* maxbits, cudaStream_t st) {
+  MES_CUDA_TRY(cudaMemsetAsync(maxbits, 0, planes * sizeof(unsigned), st));
+  const int64_t chunk = 8192;
+  dim3 g1((unsigned)((plane_size + chunk - 1) / chunk), (unsigned)planes);
+  {
+  ProfScope prof("quant_absmax", st, 0.0, 4.0 * plane_size * planes);
+  plane_absmax_kernel<<<g1, kThreads, 0, st>>>(core, plane_size, chunk, maxbits);
+  MES_LAUNCH_CHECK();
+  }
+  const int64_t total = plane_size * planes;
+  const float qmax = (float)((1 << (bits - 1)) - 1);
+  ProfScope prof("quantize", st, 0.0, 6.0 * total + 4.0 * planes);
+  quantize_kernel<<<grid_for(total, kThreads, (int64_t)sm_count() * 16), kThreads, 0, st>>>(
+      core, plane_size, total, maxbits, qmax, q, scales);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+}  // namespace mes
+
+extern "C" mes_status mes_quantize_core(const float* core, int N, const int64_t* ranks, int bits,
+                                        int16_t* q, float* scales, int status_host_sync,
+                                        void* stream) {
+  mes::clear_error();
+  if (!core || !q || !scales) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core: null pointer");
+  if (bits < 2 || bits > 16) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core: bits must be 2..16");
+  int64_t plane_size = 0, planes = 0;
+  MES_TRY(plane_shape(N, ranks, &plane_size, &planes));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::Scratch scratch(st);
+  unsigned* maxbits = nullptr;
+  MES_TRY(scratch.alloc(&maxbits, (size_t)planes));
+  MES_TRY(mes::quantize_launch(core, plane_size, planes, bits, q, scales, maxbits, st));
+  if (status_host_sync) {
+    unsigned* host = new unsigned[planes];
+    cudaError_t e = cudaMemcpyAsync(host, maxbits, planes * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      delete[] host;
+      cudaGetLastError();
+      return mes::fail(MES_ERR_CUDA, "mes_quantize_core: status read failed: %s", cudaGetErrorString(e));
+    }
+    bool finite = true;
+    for (int64_t p = 0; p < planes; ++p) finite = finite && (host[p] < 0x7f800000u);
+    delete[] host;
+    if (!finite) return mes::fail(MES_ERR_NONFINITE, "mes_quantize_core: a core plane holds NaN or Inf");
+  }
+  return MES_OK;
+}
+
+extern "C" mes_status mes_dequantize_core(const int16_t* q, const float* scales, int N,
+                                          const int64_t* ranks, float* core, void* stream) {
+  mes::clear_error();
+  if (!core || !q || !scales) return mes::fail(MES_ERR_INVALID_ARG, "mes_dequantize_core: null pointer");
+  int64_t plane_size = 0, planes = 0;
+  MES_TRY(plane_shape(N, ranks, &plane_size, &planes));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t total = plane_size * planes;
+  mes::ProfScope prof("dequantize", st, 0.0, 6.0 * total);
+  dequantize_kernel<<<mes::grid_for(total, kThreads, (int64_t)mes::sm_count() * 16), kThreads, 0, st>>>(
+      q, scales, plane_size, total, core);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}

@@ -1,0 +1,67 @@
+// Declarations of the bandwidth and small-solver kernels used by the driver.
+#pragma once
+
+#include "common.cuh"
+
+namespace mes {
+
+// A set of fibres over the trailing small modes: fibre f = f_lo + F_lo*f_hi,
+// element l of fibre f at in + f_lo*in_lo + f_hi*in_hi + l*in_l (and the
+// same for `out` with its own strides).
+struct Fibres {
+  int64_t F_lo = 1, F_hi = 1;
+  const float* in = nullptr;
+  int64_t in_lo = 0, in_hi = 0, in_l = 0;
+  float* out = nullptr;
+  int64_t out_lo = 0, out_hi = 0, out_l = 0;
+};
+
+// Kronecker product of per-mode small matrices.  op: 'T' = U^T (r x s),
+// 'N' = U (s x r), 'I' = identity (s x s).  Row index and column index are
+// multi-indices with the first small mode fastest.  K is row-major (rows x cols).
+struct KronDesc {
+  int nm = 0;
+  const float* U[6] = {nullptr};
+  int s[6] = {0};
+  int r[6] = {0};
+  char op[6] = {0};
+  int rows() const;
+  int cols() const;
+};
+mes_status kron_build(const KronDesc& d, float* K, const int* skip, cudaStream_t st);
+
+mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
+                           double* partials, int nblocks, cudaStream_t st);
+mes_status sumsq(const float* x, int64_t n, double* partials, int nblocks, const int* skip,
+                 cudaStream_t st);
+mes_status uniform_fill(float* out, int64_t n, uint64_t seed, cudaStream_t st);
+mes_status mix_fibres(const Fibres& fb, const float* Kmat, int L, int L2, const int* skip,
+                      cudaStream_t st);
+int small_gram_blocks(int64_t F);
+mes_status small_gram(const Fibres& fb, const float* Kmat, int L, int L2, int sn, int inner,
+                      double* partials, double* G, const int* skip, cudaStream_t st);
+mes_status fit_flag(const double* normX, const double* normQ, int sweep, double tol, double* hist,
+                    double* last, int* done, int* iters, cudaStream_t st);
+mes_status final_fit(const double* normX, const double* sse, double* fit, cudaStream_t st);
+mes_status col_signs(const float* U, int64_t s, int r, float* sign, cudaStream_t st);
+mes_status diag_order(const float* H, int r, int* src_of, cudaStream_t st);
+mes_status permute_cols(const float* Uin, int64_t s, int r, const int* src_of, const float* sign,
+                        float* Uout, cudaStream_t st);
+mes_status permute_core(const float* in, int64_t total, int64_t stride, int r, const int* src_of,
+                        const float* sign, float* out, cudaStream_t st);
+
+// dense.cu
+mes_status cholinv(const float* M, int r, float shift_rel, float* work, float* X, float* Rinv,
+                   int* flags, const int* skip, cudaStream_t st);
+mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,
+                     cudaStream_t st);
+mes_status eig_mid(const float* H, int r, float* Z, const int* skip, cudaStream_t st);
+
+// colour.cu / quant.cu
+mes_status colour_launch(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K, int space,
+                         float gamma, float* out, double* partials, double* norm2, cudaStream_t st);
+unsigned colour_grid(int64_t npix, int64_t K);
+mes_status quantize_launch(const float* core, int64_t plane_size, int64_t planes, int bits,
+                           int16_t* q, float* scales, unsigned* maxbits, cudaStream_t st);
+
+}  // namespace mes

@@ -1,0 +1,614 @@
+// Tucker-ALS / HOOI driver (Section III-B) and reconstruction (Eq. 1).
+//
+// Data layout.  The stack T (s1 x s2 x small modes) is first-mode fastest;
+// l indexes the trailing small modes jointly (L = prod s_n, n >= 3).  A second
+// copy XB has, per l, mode 2 fastest.  Intermediates:
+//   P  [x][q2 + r2*l]      = T x_2 S2^T             (mode-1 partial contraction)
+//   Ca [y][q1 + r1*l]      = T x_1 S1^T             (mode-2 partial contraction)
+//   B  [q1 + r1*l + r1*L*q2] = Ca x_2 S2^T          (shared by the small modes)
+// so every product below reads its operands along their contiguous index.
+//
+// Factor update of a large mode n (Eq. 8 and the text after it).  The paper
+// takes S^(n) as the leading eigenvectors of G = Y_(n) Y_(n)^T.  Forming G in
+// FP32 squares the condition number of Y_(n) and loses the trailing singular
+// directions (their eigenvalues sit below the FP32 resolution of G at these
+// sizes), so the Gram is applied in factored form: one step of block
+// subspace iteration on G is
+//     Z  = Y_(n)^T S          (the partial core),
+//     Zh = Z R_z^-1           (R_z from a shifted Cholesky of Z^T Z: keeps the
+//                              next product well conditioned),
+//     W  = Y_(n) Zh           (= G S R_z^-1: same column space as G S),
+//     S  = orth(W)            (shifted CholeskyQR, three passes),
+// warm-started from the previous sweep's factor.  Repeated steps converge to
+// the leading eigenvectors of G; the column space is what HOOI carries to the
+// next mode, and the basis is made canonical at the end.
+//
+// Small modes (colour, view x exposure) use the paper's route literally: the
+// Gram of the mode-n unfolding of Y^(n), accumulated in FP64, and its exact
+// eigenvectors (FP64 Jacobi).
+//
+// Stopping (the paper is silent): after sweep t the fit
+// 1 - sqrt(||T||^2 - ||Q||^2)/||T|| is compared with the previous one; a
+// device flag set when |change| < tol turns every later sweep's kernels into
+// no-ops, so the host enqueues max_iters sweeps without reading anything back.
+// The returned fit is recomputed from the explicit residual ||T - T_hat||,
+// which does not suffer the cancellation of ||T||^2 - ||Q||^2 in FP32.
+#include <cstring>
+
+#include "gemm.cuh"
+#include "small.cuh"
+
+namespace {
+
+using mes::Gemm;
+using mes::Fibres;
+using mes::KronDesc;
+
+constexpr float kShiftZ = 1e-7f;   // relative shift of the Z-preconditioning Cholesky
+constexpr float kShiftW = 1e-6f;   // relative shift of the first CholeskyQR pass
+
+struct Shape {
+  int N = 0;
+  int64_t s[8] = {0}, r[8] = {0};
+  int64_t s1 = 1, s2 = 1, r1 = 1, r2 = 1;
+  int nsm = 0;
+  int64_t L = 1, Lr = 1;
+  bool small_full = true;
+};
+
+mes_status make_shape(int N, const int64_t* dims, const int64_t* ranks, Shape* sh, const char* who) {
+  if (N < 2 || N > 8) return mes::fail(MES_ERR_INVALID_ARG, "%s: N must be 2..8 (got %d)", who, N);
+  if (!dims || !ranks) return mes::fail(MES_ERR_INVALID_ARG, "%s: null dims or ranks", who);
+  sh->N = N;
+  for (int n = 0; n < N; ++n) {
+    sh->s[n] = dims[n];
+    sh->r[n] = ranks[n];
+    if (dims[n] < 1) return mes::fail(MES_ERR_INVALID_ARG, "%s: dims[%d] < 1", who, n);
+    if (ranks[n] < 1 || ranks[n] > dims[n])
+      return mes::fail(MES_ERR_RANK, "%s: ranks[%d]=%lld outside 1..%lld", who, n, (long long)ranks[n],
+                       (long long)dims[n]);
+  }
+  for (int n = 0; n < N; ++n) {
+    double prod = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != n) prod *= (double)ranks[m];
+    if ((double)ranks[n] > prod)
+      return mes::fail(MES_ERR_RANK, "%s: ranks[%d] exceeds the product of the other ranks", who, n);
+  }
+  sh->s1 = dims[0];
+  sh->s2 = dims[1];
+  sh->r1 = ranks[0];
+  sh->r2 = ranks[1];
+  sh->nsm = N - 2;
+  sh->L = 1;
+  sh->Lr = 1;
+  sh->small_full = true;
+  for (int n = 2; n < N; ++n) {
+    if (dims[n] > 32) return mes::fail(MES_ERR_INVALID_ARG, "%s: modes 3..N must have size <= 32", who);
+    sh->L *= dims[n];
+    sh->Lr *= ranks[n];
+    if (ranks[n] != dims[n]) sh->small_full = false;
+  }
+  if (sh->L > 1024) return mes::fail(MES_ERR_INVALID_ARG, "%s: product of modes 3..N above 1024", who);
+  if (sh->L * sh->L > 16384)
+    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "%s: product of modes 3..N above 128", who);
+  if (sh->r1 > 1024 || sh->r2 > 1024)
+    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "%s: ranks of modes 1, 2 above 1024", who);
+  return MES_OK;
+}
+
+Gemm base() { return Gemm(); }
+
+struct Driver {
+  Shape sh;
+  cudaStream_t st;
+  mes::Scratch* scr;
+  const int* skip = nullptr;       // device stop flag, null outside the sweeps
+  int* flags = nullptr;            // numerics flags (cholinv pivots)
+
+  float *cwA = nullptr, *cwX = nullptr, *H = nullptr, *Rinv = nullptr;
+  float *W = nullptr, *W2 = nullptr, *Z = nullptr, *Zh = nullptr, *Kmat = nullptr;
+  double *gpart = nullptr, *G64 = nullptr;
+
+  mes_status gemm(const Gemm& g) {
+    Gemm h = g;
+    h.skip = skip;
+    return mes::gemm_f32(h, st);
+  }
+
+  // S (s x r) := orth(W) by three passes of CholeskyQR, the first shifted.
+  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout) {
+    float* src = Win;
+    float* bufs[2] = {W2, Win};
+    for (int pass = 0; pass < 3; ++pass) {
+      float* dst = (pass == 2) ? Sout : bufs[pass & 1];
+      Gemm g = base();  // H = src^T src
+      g.M = r; g.N = r; g.K_lo = s;
+      g.A = src; g.a_m = s; g.a_k = 1;
+      g.B = src; g.b_n = s; g.b_k = 1;
+      g.C = H; g.c_m = 1; g.c_n = r;
+      MES_TRY(gemm(g));
+      MES_TRY(mes::cholinv(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, cwX, Rinv, flags, skip, st));
+      Gemm a = base();  // dst = src * Rinv
+      a.M = s; a.N = r; a.K_lo = r;
+      a.A = src; a.a_m = 1; a.a_k = s;
+      a.B = Rinv; a.b_n = r; a.b_k = 1;
+      a.C = dst; a.c_m = 1; a.c_n = s;
+      MES_TRY(gemm(a));
+      src = dst;
+    }
+    return MES_OK;
+  }
+
+  // One subspace step for a large mode: Y is given through two GEMM operand
+  // descriptions (Yt: Z = Y^T S,  Yn: W = Y Zh), J = number of columns of Y_(n).
+  mes_status subspace_step(const Gemm& zdesc, const Gemm& wdesc, int64_t J, int64_t s, int64_t r,
+                           float* S) {
+    // Z = Y^T S   (J x r, stored Z[j + J*q])
+    Gemm gz = zdesc;
+    gz.B = S; gz.b_n = s; gz.b_k = 1;
+    gz.C = Z; gz.c_m = 1; gz.c_n = J;
+    MES_TRY(gemm(gz));
+    // H = Z^T Z, R_z, Zh = Z R_z^-1
+    Gemm gh = base();
+    gh.M = r; gh.N = r; gh.K_lo = J;
+    gh.A = Z; gh.a_m = J; gh.a_k = 1;
+    gh.B = Z; gh.b_n = J; gh.b_k = 1;
+    gh.C = H; gh.c_m = 1; gh.c_n = r;
+    MES_TRY(gemm(gh));
+    MES_TRY(mes::cholinv(H, (int)r, kShiftZ, cwA, cwX, Rinv, flags, skip, st));
+    Gemm ga = base();
+    ga.M = J; ga.N = r; ga.K_lo = r;
+    ga.A = Z; ga.a_m = 1; ga.a_k = J;
+    ga.B = Rinv; ga.b_n = r; ga.b_k = 1;
+    ga.C = Zh; ga.c_m = 1; ga.c_n = J;
+    MES_TRY(gemm(ga));
+    // W = Y Zh   (s x r)
+    Gemm gw = wdesc;
+    gw.C = W; gw.c_m = 1; gw.c_n = s;
+    MES_TRY(gemm(gw));
+    return orth(W, s, r, S);
+  }
+
+  // Small-mode Gram (FP64) of fibres projected by the Kronecker matrix built
+  // from `kd`, then its leading eigenvectors into U (s_n x r_n).
+  mes_status small_update(const Fibres& fb, const KronDesc& kd, int which, float* U) {
+    MES_TRY(mes::kron_build(kd, Kmat, skip, st));
+    int inner = 1;
+    for (int m = 0; m < which; ++m) inner *= (kd.op[m] == 'T') ? kd.r[m] : kd.s[m];
+    const int sn = kd.s[which];
+    MES_TRY(mes::small_gram(fb, Kmat, kd.cols(), kd.rows(), sn, inner, gpart, G64, skip, st));
+    return mes::eig_small(G64, sn, kd.r[which], U, nullptr, skip, st);
+  }
+};
+
+// Reconstruction T_hat = Q x_1 S1 x_2 S2 x_{n>=3} S_n (Eq. 1): the small
+// modes by fibre mixing, then mode 2, then mode 1 with an optional fused
+// residual against `ref`.
+mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float* const* fac, float* out,
+                                const float* ref, double* sse, mes::Scratch& scr, float* T1, float* T2,
+                                float* Kmat, cudaStream_t st) {
+  const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
+  // T1[q2 + r2 q1 + r1 r2 l] = (Q x_{n>=3} S_n)
+  KronDesc kd;
+  kd.nm = sh.nsm;
+  for (int m = 0; m < sh.nsm; ++m) {
+    kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'N'; kd.U[m] = fac[m + 2];
+  }
+  MES_TRY(mes::kron_build(kd, Kmat, nullptr, st));
+  Fibres fb;
+  fb.F_lo = r1; fb.F_hi = r2;
+  fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
+  fb.out = T1; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
+  MES_TRY(mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st));
+  // T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2[y + s2 q2]
+  Gemm g = Gemm();
+  g.M = r1; g.N = s2; g.K_lo = r2; g.batch = (int)L;
+  g.A = T1; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
+  g.B = fac[1]; g.b_n = 1; g.b_k = s2; g.b_b = 0;
+  g.C = T2; g.c_m = 1; g.c_n = r1; g.c_b = r1 * s2;
+  MES_TRY(mes::gemm_f32(g, st));
+  // out[x + s1 n] = sum_q1 S1[x + s1 q1] T2[q1 + r1 n],  n = y + s2 l
+  Gemm h = Gemm();
+  h.M = s1; h.N = s2 * L; h.K_lo = r1;
+  h.A = fac[0]; h.a_m = 1; h.a_k = s1;
+  h.B = T2; h.b_n = r1; h.b_k = 1;
+  h.C = out; h.c_m = 1; h.c_n = s1;
+  if (ref && sse && !out) {
+    double* part = nullptr;
+    const int64_t np = mes::gemm_partials(h);
+    MES_TRY(scr.alloc(&part, np));
+    h.ref = ref;
+    h.C = nullptr;
+    h.partials = part;
+    MES_TRY(mes::gemm_f32(h, st));
+    MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
+    return MES_OK;
+  }
+  MES_TRY(mes::gemm_f32(h, st));
+  if (ref && sse) {
+    // the residual is a second pass of the same product in residual mode
+    double* part = nullptr;
+    const int64_t np = mes::gemm_partials(h);
+    MES_TRY(scr.alloc(&part, np));
+    h.ref = ref;
+    h.partials = part;
+    MES_TRY(mes::gemm_f32(h, st));
+    MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
+  }
+  return MES_OK;
+}
+
+}  // namespace
+
+extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
+                                     int max_iters, double tol, float* core, float* const* factors,
+                                     double* fit, const mes_als_opts* opts, void* stream) {
+  mes::clear_error();
+  Shape sh;
+  MES_TRY(make_shape(N, dims, ranks, &sh, "mes_tucker_als"));
+  if (!X || !core || !factors) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: null pointer");
+  for (int n = 0; n < N; ++n)
+    if (!factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: factors[%d] is null", n);
+  if (max_iters < 1) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: max_iters must be >= 1");
+  if (!(tol >= 0.0)) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: tol must be >= 0");
+  mes_als_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  const int precision = o.precision;
+  if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_BF16X3)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: unknown precision %d", precision);
+  if (precision != MES_PREC_FP32)
+    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "mes_tucker_als: tensor-core precision forms not built");
+  const int init_iters = o.init_iters > 0 ? o.init_iters : 4;
+  const int inner_iters = o.inner_iters > 0 ? o.inner_iters : 2;
+  const uint64_t seed = o.seed ? o.seed : 1;
+  const bool canonical = o.canonical >= 0;
+  if (o.init_iters < 0 || o.inner_iters < 0)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: negative iteration option");
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::AuditScope audit_scope;
+  {
+    int64_t nX = 1, nQ = 1;
+    for (int n = 0; n < N; ++n) { nX *= sh.s[n]; nQ *= sh.r[n]; }
+    mes::audit_register(X, (size_t)nX * 4);
+    mes::audit_register(core, (size_t)nQ * 4);
+    for (int n = 0; n < N; ++n) mes::audit_register(factors[n], (size_t)(sh.s[n] * sh.r[n]) * 4);
+  }
+  mes::Scratch scr(st);
+  Driver d;
+  d.sh = sh;
+  d.st = st;
+  d.scr = &scr;
+
+  const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
+  const int64_t rmax = r1 > r2 ? r1 : r2;
+  const int64_t nel = s1 * s2 * L;
+  const int64_t J0 = r2 * Lr, J1 = r1 * Lr;     // columns of Y^(1)_(1), Y^(2)_(2)
+  int64_t zsz = s2 * L * r1;
+  if (s1 * L * r2 > zsz) zsz = s1 * L * r2;
+  if (r1 * r2 * Lr > zsz) zsz = r1 * r2 * Lr;
+
+  float *XB, *P, *Ca, *Bt, *Y0 = nullptr, *Y1 = nullptr, *ctmp, *T1, *T2;
+  double *normX, *normQ, *sse, *xpart, *qpart, *fitlast;
+  int *done, *flags;
+  float* sign;
+  int* order;
+  const int nblk = (int)mes::grid_for(nel, 256, (int64_t)mes::sm_count() * 4);
+  MES_TRY(scr.alloc(&XB, nel));
+  MES_TRY(scr.alloc(&P, s1 * r2 * L));
+  MES_TRY(scr.alloc(&Ca, s2 * r1 * L));
+  MES_TRY(scr.alloc(&Bt, r1 * L * r2));
+  if (!sh.small_full) {
+    MES_TRY(scr.alloc(&Y0, s1 * J0));
+    MES_TRY(scr.alloc(&Y1, s2 * J1));
+  }
+  MES_TRY(scr.alloc(&ctmp, r1 * r2 * Lr));
+  MES_TRY(scr.alloc(&T1, r1 * r2 * L));
+  MES_TRY(scr.alloc(&T2, r1 * s2 * L));
+  MES_TRY(scr.alloc(&d.Z, zsz));
+  MES_TRY(scr.alloc(&d.Zh, zsz));
+  MES_TRY(scr.alloc(&d.W, (s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2)));
+  MES_TRY(scr.alloc(&d.W2, (s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2)));
+  MES_TRY(scr.alloc(&d.H, rmax * rmax));
+  MES_TRY(scr.alloc(&d.Rinv, rmax * rmax));
+  MES_TRY(scr.alloc(&d.cwA, rmax * rmax));
+  MES_TRY(scr.alloc(&d.cwX, rmax * rmax));
+  MES_TRY(scr.alloc(&d.Kmat, 16384));
+  MES_TRY(scr.alloc(&d.gpart, (size_t)mes::small_gram_blocks(s1 * s2) * 1024));
+  MES_TRY(scr.alloc(&d.G64, 1024));
+  MES_TRY(scr.alloc(&normX, 1));
+  MES_TRY(scr.alloc(&normQ, 1));
+  MES_TRY(scr.alloc(&sse, 1));
+  MES_TRY(scr.alloc(&fitlast, 1));
+  MES_TRY(scr.alloc(&xpart, nblk));
+  MES_TRY(scr.alloc(&qpart, nblk));
+  MES_TRY(scr.alloc(&done, 2));
+  flags = done + 1;
+  MES_TRY(scr.alloc(&sign, rmax));
+  MES_TRY(scr.alloc(&order, rmax));
+  d.flags = flags;
+  MES_CUDA_TRY(cudaMemsetAsync(done, 0, 2 * sizeof(int), st));
+  if (o.iters_done) MES_CUDA_TRY(cudaMemsetAsync(o.iters_done, 0, sizeof(int), st));
+
+  float* U0 = factors[0];
+  float* U1 = factors[1];
+
+  // ---- second layout of T and ||T||^2 ----
+  MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st));
+  MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
+
+  // ---- initialisation: truncated HOSVD (Eq. 6, Eq. 7) or given factors ----
+  if (o.init_factors) {
+    for (int n = 0; n < N; ++n) {
+      if (!o.init_factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: init_factors[%d] null", n);
+      MES_CUDA_TRY(cudaMemcpyAsync(factors[n], o.init_factors[n], sizeof(float) * sh.s[n] * sh.r[n],
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+  } else {
+    // small modes: exact eigenvectors of the unfolding Grams of T
+    for (int n = 2; n < N; ++n) {
+      KronDesc kd;
+      kd.nm = sh.nsm;
+      for (int m = 0; m < sh.nsm; ++m) {
+        kd.s[m] = (int)sh.s[m + 2];
+        kd.r[m] = (int)sh.r[m + 2];
+        kd.op[m] = 'I';
+        kd.U[m] = nullptr;
+      }
+      Fibres fb;
+      fb.F_lo = s1 * s2; fb.F_hi = 1;
+      fb.in = X; fb.in_lo = 1; fb.in_hi = 0; fb.in_l = s1 * s2;
+      MES_TRY(d.small_update(fb, kd, n - 2, factors[n]));
+    }
+    // mode 1: T_(1) = rows x, columns (y, l); mode 2: rows y, columns (x, l)
+    for (int n = 0; n < 2; ++n) {
+      const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
+      float* S = factors[n];
+      MES_TRY(mes::uniform_fill(d.W, s * r, seed * 2 + n, st));
+      MES_TRY(d.orth(d.W, s, r, S));
+      Gemm gz = base(), gw = base();
+      int64_t J;
+      if (n == 0) {
+        J = s2 * L;   // Z[(y,l)][q] = sum_x T[x + s1*(y,l)] S[x,q]
+        gz.M = J; gz.N = r; gz.K_lo = s1;
+        gz.A = X; gz.a_m = s1; gz.a_k = 1;
+        // W[x][q] = sum_{y,l} XB[y + s2*x + s1*s2*l] Zh[(y + s2*l) + J*q]
+        gw.M = s1; gw.N = r; gw.K_lo = s2; gw.K_hi = L;
+        gw.A = XB; gw.a_m = s2; gw.a_k = 1; gw.a_kh = s1 * s2;
+        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s2;
+      } else {
+        J = s1 * L;   // Z[(x,l)][q] = sum_y XB[y + s2*(x + s1*l)] S[y,q]
+        gz.M = J; gz.N = r; gz.K_lo = s2;
+        gz.A = XB; gz.a_m = s2; gz.a_k = 1;
+        // W[y][q] = sum_{x,l} X[x + s1*y + s1*s2*l] Zh[(x + s1*l) + J*q]
+        gw.M = s2; gw.N = r; gw.K_lo = s1; gw.K_hi = L;
+        gw.A = X; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
+        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s1;
+      }
+      for (int it = 0; it < init_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s, r, S));
+    }
+  }
+
+  // ---- sweeps (Eq. 8), n = 1..N ----
+  d.skip = done;
+  for (int sweep = 1; sweep <= max_iters; ++sweep) {
+    // mode 1: P = T x_2 S2^T, per l: P[x][q2 + r2 l] = sum_y XB[y + s2 x + s1 s2 l] U1[y + s2 q2]
+    {
+      Gemm g = base();
+      g.M = s1; g.N = r2; g.K_lo = s2; g.batch = (int)L;
+      g.A = XB; g.a_m = s2; g.a_k = 1; g.a_b = s1 * s2;
+      g.B = U1; g.b_n = s2; g.b_k = 1; g.b_b = 0;
+      g.C = P; g.c_m = r2 * L; g.c_n = 1; g.c_b = r2;
+      MES_TRY(d.gemm(g));
+      const float* Y = P;
+      if (!sh.small_full) {
+        KronDesc kd;
+        kd.nm = sh.nsm;
+        for (int m = 0; m < sh.nsm; ++m) {
+          kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'T'; kd.U[m] = factors[m + 2];
+        }
+        MES_TRY(mes::kron_build(kd, d.Kmat, done, st));
+        Fibres fb;
+        fb.F_lo = r2; fb.F_hi = s1;
+        fb.in = P; fb.in_lo = 1; fb.in_hi = r2 * L; fb.in_l = r2;
+        fb.out = Y0; fb.out_lo = 1; fb.out_hi = J0; fb.out_l = r2;
+        MES_TRY(mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, done, st));
+        Y = Y0;
+      }
+      const int64_t J = sh.small_full ? r2 * L : J0;
+      Gemm gz = base(), gw = base();
+      gz.M = J; gz.N = r1; gz.K_lo = s1;          // Z[j][q] = sum_x Y[j + J x] S[x][q]
+      gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      gw.M = s1; gw.N = r1; gw.K_lo = J;          // W[x][q] = sum_j Y[j + J x] Zh[j + J q]
+      gw.A = Y; gw.a_m = J; gw.a_k = 1;
+      gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
+      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s1, r1, U0));
+    }
+    // mode 2: Ca = T x_1 S1^T: Ca[(q1 + r1 l) + r1 L y] = sum_x U0[x + s1 q1] X[x + s1 (y + s2 l)]
+    {
+      Gemm g = base();
+      g.M = r1; g.N = s2 * L; g.K_lo = s1;
+      g.A = U0; g.a_m = s1; g.a_k = 1;
+      g.B = X; g.b_n = s1; g.b_k = 1;
+      g.C = Ca; g.c_m = 1; g.N_lo = s2; g.c_n = r1 * L; g.c_nh = r1;
+      MES_TRY(d.gemm(g));
+      const float* Y = Ca;
+      if (!sh.small_full) {
+        KronDesc kd;
+        kd.nm = sh.nsm;
+        for (int m = 0; m < sh.nsm; ++m) {
+          kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'T'; kd.U[m] = factors[m + 2];
+        }
+        MES_TRY(mes::kron_build(kd, d.Kmat, done, st));
+        Fibres fb;
+        fb.F_lo = r1; fb.F_hi = s2;
+        fb.in = Ca; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
+        fb.out = Y1; fb.out_lo = 1; fb.out_hi = J1; fb.out_l = r1;
+        MES_TRY(mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, done, st));
+        Y = Y1;
+      }
+      const int64_t J = sh.small_full ? r1 * L : J1;
+      Gemm gz = base(), gw = base();
+      gz.M = J; gz.N = r2; gz.K_lo = s2;
+      gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      gw.M = s2; gw.N = r2; gw.K_lo = J;
+      gw.A = Y; gw.a_m = J; gw.a_k = 1;
+      gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
+      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1));
+    }
+    // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Ca[(q1 + r1 l) + r1 L y] U1[y + s2 q2]
+    {
+      Gemm g = base();
+      g.M = r1 * L; g.N = r2; g.K_lo = s2;
+      g.A = Ca; g.a_m = 1; g.a_k = r1 * L;
+      g.B = U1; g.b_n = s2; g.b_k = 1;
+      g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
+      MES_TRY(d.gemm(g));
+    }
+    // small modes n = 3..N: Gram of B x_{m != n} S_m^T, exact eigenvectors
+    for (int n = 2; n < N; ++n) {
+      KronDesc kd;
+      kd.nm = sh.nsm;
+      for (int m = 0; m < sh.nsm; ++m) {
+        kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2];
+        kd.op[m] = (m + 2 == n) ? 'I' : 'T';
+        kd.U[m] = factors[m + 2];
+      }
+      Fibres fb;
+      fb.F_lo = r1; fb.F_hi = r2;
+      fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
+      MES_TRY(d.small_update(fb, kd, n - 2, factors[n]));
+    }
+    // core Q = B x_{n>=3} S_n^T (Eq. 5 / Eq. 7 with the current factors)
+    {
+      KronDesc kd;
+      kd.nm = sh.nsm;
+      for (int m = 0; m < sh.nsm; ++m) {
+        kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'T'; kd.U[m] = factors[m + 2];
+      }
+      MES_TRY(mes::kron_build(kd, d.Kmat, done, st));
+      Fibres fb;
+      fb.F_lo = r1; fb.F_hi = r2;
+      fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
+      fb.out = core; fb.out_lo = 1; fb.out_hi = r1; fb.out_l = r1 * r2;
+      MES_TRY(mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, done, st));
+      MES_TRY(mes::sumsq(core, r1 * r2 * Lr, qpart, nblk, done, st));
+      MES_TRY(mes::sum_doubles(qpart, nblk, normQ, done, st));
+      MES_TRY(mes::fit_flag(normX, normQ, sweep, tol, o.fit_history, fitlast, done, o.iters_done, st));
+    }
+  }
+  d.skip = nullptr;
+
+  // ---- canonical basis of the large modes ----
+  if (canonical) {
+    const int64_t ncore = r1 * r2 * Lr;
+    for (int n = 0; n < 2; ++n) {
+      const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
+      float* S = factors[n];
+      Gemm gh = base();   // H = Q_(n) Q_(n)^T
+      gh.M = r; gh.N = r; gh.C = d.H; gh.c_m = 1; gh.c_n = r;
+      if (n == 0) {
+        gh.K_lo = r2 * Lr;
+        gh.A = core; gh.a_m = 1; gh.a_k = r1;
+        gh.B = core; gh.b_n = 1; gh.b_k = r1;
+      } else {
+        gh.K_lo = r1; gh.K_hi = Lr;
+        gh.A = core; gh.a_m = r1; gh.a_k = 1; gh.a_kh = r1 * r2;
+        gh.B = core; gh.b_n = r1; gh.b_k = 1; gh.b_kh = r1 * r2;
+      }
+      MES_TRY(d.gemm(gh));
+      const int64_t stride = n == 0 ? 1 : r1;
+      if (r <= 128) {
+        // Z = eigenvectors of H (FP32 Jacobi), then one CholeskyQR pass on Z
+        // so the rotation is orthogonal to FP32 precision: the accumulated
+        // Jacobi rotations drift by ~sqrt(#rotations) ulp.
+        MES_TRY(mes::eig_mid(d.H, (int)r, d.cwX, nullptr, st));
+        Gemm gzz = base();
+        gzz.M = r; gzz.N = r; gzz.K_lo = r;
+        gzz.A = d.cwX; gzz.a_m = r; gzz.a_k = 1;
+        gzz.B = d.cwX; gzz.b_n = r; gzz.b_k = 1;
+        gzz.C = d.H; gzz.c_m = 1; gzz.c_n = r;
+        MES_TRY(d.gemm(gzz));
+        MES_TRY(mes::cholinv(d.H, (int)r, 0.f, d.cwA, d.Rinv, d.W2, flags, nullptr, st));
+        Gemm gzr = base();
+        gzr.M = r; gzr.N = r; gzr.K_lo = r;
+        gzr.A = d.cwX; gzr.a_m = 1; gzr.a_k = r;
+        gzr.B = d.W2; gzr.b_n = r; gzr.b_k = 1;
+        gzr.C = d.Rinv; gzr.c_m = 1; gzr.c_n = r;
+        MES_TRY(d.gemm(gzr));                                       // Z in Rinv
+        Gemm gu = base();  // W = S Z
+        gu.M = s; gu.N = r; gu.K_lo = r;
+        gu.A = S; gu.a_m = 1; gu.a_k = s;
+        gu.B = d.Rinv; gu.b_n = r; gu.b_k = 1;
+        gu.C = d.W; gu.c_m = 1; gu.c_n = s;
+        MES_TRY(d.gemm(gu));
+        MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
+        Gemm gq = base();  // Q <- Q x_n Z^T
+        if (n == 0) {
+          gq.M = r1; gq.N = r2 * Lr; gq.K_lo = r1;
+          gq.A = d.Rinv; gq.a_m = r1; gq.a_k = 1;
+          gq.B = core; gq.b_n = r1; gq.b_k = 1;
+          gq.C = ctmp; gq.c_m = 1; gq.c_n = r1;
+        } else {
+          gq.M = r1; gq.N = r2; gq.K_lo = r2; gq.batch = (int)Lr;
+          gq.A = core; gq.a_m = 1; gq.a_k = r1; gq.a_b = r1 * r2;
+          gq.B = d.Rinv; gq.b_n = r2; gq.b_k = 1;
+          gq.C = ctmp; gq.c_m = 1; gq.c_n = r1; gq.c_b = r1 * r2;
+        }
+        MES_TRY(d.gemm(gq));
+        MES_CUDA_TRY(cudaMemcpyAsync(core, ctmp, sizeof(float) * ncore, cudaMemcpyDeviceToDevice, st));
+      } else {
+        MES_TRY(mes::diag_order(d.H, (int)r, order, st));
+        MES_TRY(mes::permute_cols(S, s, (int)r, order, nullptr, d.W, st));
+        MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
+        MES_TRY(mes::permute_core(core, ncore, stride, (int)r, order, nullptr, ctmp, st));
+        MES_CUDA_TRY(cudaMemcpyAsync(core, ctmp, sizeof(float) * ncore, cudaMemcpyDeviceToDevice, st));
+      }
+      MES_TRY(mes::col_signs(S, s, (int)r, sign, st));
+      MES_TRY(mes::permute_cols(S, s, (int)r, nullptr, sign, d.W, st));
+      MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
+      MES_TRY(mes::permute_core(core, ncore, stride, (int)r, nullptr, sign, ctmp, st));
+      MES_CUDA_TRY(cudaMemcpyAsync(core, ctmp, sizeof(float) * ncore, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+
+  // ---- fit from the explicit residual ----
+  if (fit) {
+    const float* fac[8];
+    for (int n = 0; n < N; ++n) fac[n] = factors[n];
+    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st));
+    MES_TRY(mes::final_fit(normX, sse, fit, st));
+  }
+  return MES_OK;
+}
+
+extern "C" mes_status mes_reconstruct(const float* core, const float* const* factors, int N,
+                                      const int64_t* dims, const int64_t* ranks, float* out,
+                                      const float* ref, double* sse, void* stream) {
+  mes::clear_error();
+  Shape sh;
+  MES_TRY(make_shape(N, dims, ranks, &sh, "mes_reconstruct"));
+  if (!core || !factors || !out) return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: null pointer");
+  for (int n = 0; n < N; ++n)
+    if (!factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: factors[%d] is null", n);
+  if ((ref == nullptr) != (sse == nullptr))
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: ref and sse go together");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::AuditScope audit_scope;
+  {
+    int64_t nX = 1, nQ = 1;
+    for (int n = 0; n < N; ++n) { nX *= sh.s[n]; nQ *= sh.r[n]; }
+    mes::audit_register(out, (size_t)nX * 4);
+    if (ref) mes::audit_register(ref, (size_t)nX * 4);
+    mes::audit_register(core, (size_t)nQ * 4);
+    for (int n = 0; n < N; ++n) mes::audit_register(factors[n], (size_t)(sh.s[n] * sh.r[n]) * 4);
+  }
+  mes::Scratch scr(st);
+  float *T1, *T2, *Kmat;
+  MES_TRY(scr.alloc(&T1, sh.r1 * sh.r2 * sh.L));
+  MES_TRY(scr.alloc(&T2, sh.r1 * sh.s2 * sh.L));
+  MES_TRY(scr.alloc(&Kmat, 16384));
+  return mes_reconstruct_impl(sh, core, factors, out, ref, sse, scr, T1, T2, Kmat, st);
+}

@@ -1,0 +1,156 @@
+// Error buffer, device queries and the version string.
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mes {
+
+static thread_local char g_err[1024] = "";
+
+mes_status fail(mes_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+struct Region {
+  uintptr_t lo, hi;
+};
+static thread_local Region g_regions[128];
+static thread_local int g_nregions = 0;
+
+void audit_register(const void* p, size_t bytes) {
+  if (!p || g_nregions >= 128) return;
+  g_regions[g_nregions++] = Region{(uintptr_t)p, (uintptr_t)p + bytes};
+}
+
+void audit_clear() { g_nregions = 0; }
+
+mes_status audit(const void* p, size_t last_byte, const char* what) {
+  if (!p) return MES_OK;
+  const uintptr_t a = (uintptr_t)p;
+  for (int i = 0; i < g_nregions; ++i) {
+    if (a >= g_regions[i].lo && a < g_regions[i].hi) {
+      if (a + last_byte >= g_regions[i].hi)
+        return fail(MES_ERR_INVALID_ARG, "bounds audit: %s reaches byte %zu of a %zu-byte buffer", what,
+                    (size_t)(a - g_regions[i].lo) + last_byte, (size_t)(g_regions[i].hi - g_regions[i].lo));
+      return MES_OK;
+    }
+  }
+  return MES_OK;
+}
+
+// ---- profiler ----
+struct ProfRec {
+  int fam;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+static size_t g_pool_used = 0;
+static std::vector<std::string> g_fams;
+static cudaEvent_t g_pending = nullptr;
+
+static cudaEvent_t pool_event() {
+  if (g_pool_used == g_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_used++];
+}
+
+bool prof_on() { return g_prof; }
+
+void prof_begin(cudaStream_t st) {
+  g_pending = pool_event();
+  if (g_pending) cudaEventRecord(g_pending, st);
+}
+
+void prof_end(const char* family, cudaStream_t st, double flops, double bytes) {
+  cudaEvent_t b = pool_event();
+  if (!g_pending || !b) return;
+  cudaEventRecord(b, st);
+  int fam = -1;
+  for (size_t i = 0; i < g_fams.size(); ++i)
+    if (g_fams[i] == family) fam = (int)i;
+  if (fam < 0) {
+    g_fams.push_back(family);
+    fam = (int)g_fams.size() - 1;
+  }
+  g_recs.push_back(ProfRec{fam, g_pending, b, flops, bytes});
+  g_pending = nullptr;
+}
+
+}  // namespace mes
+
+extern "C" void mes_profile_enable(int on) {
+  mes::g_prof = on != 0;
+  if (on) {
+    mes::g_recs.clear();
+    mes::g_fams.clear();
+    mes::g_pool_used = 0;
+  }
+}
+
+extern "C" int mes_profile_count(void) { return (int)mes::g_fams.size(); }
+
+extern "C" mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, double* ms,
+                                      double* flops, double* bytes) {
+  if (i < 0 || i >= (int)mes::g_fams.size() || !name || name_len < 2)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_profile_get: bad index or buffer");
+  snprintf(name, (size_t)name_len, "%s", mes::g_fams[i].c_str());
+  int64_t n = 0;
+  double t = 0.0, f = 0.0, b = 0.0;
+  for (const auto& r : mes::g_recs) {
+    if (r.fam != i) continue;
+    float e = 0.f;
+    cudaError_t err = cudaEventSynchronize(r.b);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&e, r.a, r.b);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return mes::fail(MES_ERR_CUDA, "mes_profile_get: %s", cudaGetErrorString(err));
+    }
+    ++n;
+    t += e;
+    f += r.flops;
+    b += r.bytes;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  if (bytes) *bytes = b;
+  return MES_OK;
+}
+
+extern "C" const char* mes_last_error(void) { return mes::g_err; }
+
+extern "C" const char* mes_version(void) { return "mes 0.1.0 sm_103a"; }

@@ -196,3 +196,20 @@ def test_psnr_definition():
     Xh = X + 0.01
     # peak = max - min = 1, mse = 1e-4  ->  40 dB
     assert abs(tucker.psnr(X, Xh) - 40.0) < 1e-9
+
+
+def test_element_wise_model_matches_reconstruction():
+    rng = np.random.default_rng(15)
+    core = rng.standard_normal((3, 2, 2, 3))
+    Us = [rng.standard_normal((s, r)) for s, r in zip((5, 4, 3, 4), core.shape)]
+    full = tucker.reconstruct(core, Us)
+    for idx in [(0, 0, 0, 0), (4, 3, 2, 3), (2, 1, 0, 2)]:
+        # brute-force sum of Eq. 2
+        want = 0.0
+        for q in itertools.product(*[range(r) for r in core.shape]):
+            term = core[q]
+            for U, t, qq in zip(Us, idx, q):
+                term *= U[t, qq]
+            want += term
+        assert abs(tucker.element(core, Us, idx) - want) < 1e-12
+        assert abs(full[idx] - want) < 1e-12
