@@ -199,6 +199,19 @@ int mes_profile_count(void);
 mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, double* ms,
                            double* flops, double* bytes);
 
+/*
+ * Test hook for the library's matrix-product kernels (no counterpart in the
+ * paper; used by the test suite to check each kernel in isolation).
+ * C[b][m][n] = sum_k A[b][m][k] * B[b][n][k], all row-major FP32 device
+ * arrays, batch >= 1.  impl 0: CUDA-core FP32 kernel; 1: tcgen05 kind::tf32;
+ * 2: tcgen05 kind::f16 on BF16-rounded copies of A and B.  Synchronises the
+ * stream.  MES_ERR_INVALID_ARG for bad sizes or operands the tensor-core
+ * kernel cannot address (row strides must be multiples of 16 bytes);
+ * MES_ERR_TIMEOUT if a bounded pipeline wait gave up.
+ */
+mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M, int64_t N,
+                             int64_t K, int batch, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,165 +46,182 @@ cholinv_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __r
     dinv[i] = 1.f / d;
   }
   __syncthreads();
-  const float shift = shift_rel * (float)r;
-  // A = D^-1 M D^-1 + shift I  (lower triangle, column-major)
-  for (int64_t e = t; e < (int64_t)r * r; e += kChol) {
-    int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
-    if (i >= j) {
-      float v = Min[e] * dinv[i] * dinv[j];
-      if (i == j) v += shift;
-      A[e] = v;
+  // Shifted Cholesky with restarts: the shift must dominate the FP32
+  // rounding of the Gram (else a pivot goes non-positive) yet stay small (the
+  // next unshifted pass needs W * Rinv well conditioned).  Start at
+  // shift_rel and, when a pivot falls below the floor, restart with a ten
+  // times larger relative shift (at most 1e-2).
+  __shared__ int bad;
+  float rel = shift_rel;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const float shift = rel * (float)r;
+    const float floor = fmaxf(1e-7f, 0.1f * shift);
+    if (t == 0) bad = 0;
+    // A = D^-1 M D^-1 + shift I  (lower triangle, column-major)
+    for (int64_t e = t; e < (int64_t)r * r; e += kChol) {
+      int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
+      if (i >= j) {
+        float v = Min[e] * dinv[i] * dinv[j];
+        if (i == j) v += shift;
+        A[e] = v;
+      }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ---- blocked right-looking Cholesky, lower, in place in A ----
-  for (int p0 = 0; p0 < r; p0 += PB) {
-    const int b = min(PB, r - p0);
-    for (int e = t; e < b * b; e += kChol) {
-      int i = e % b, j = e / b;
-      Dg[i * (PB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int j = 0; j < b; ++j) {
-        float piv = Dg[j * (PB + 1) + j];
-        if (!(piv > 1e-6f)) {
-          if (lane == 0 && flags) atomicOr(flags, 1);
-          piv = 1e-6f;
-        }
-        piv = sqrtf(piv);
-        __syncwarp();
-        if (lane == j) Dg[j * (PB + 1) + j] = piv;
-        if (lane > j && lane < b) Dg[lane * (PB + 1) + j] /= piv;
-        __syncwarp();
-        if (lane > j && lane < b) {
-          float lij = Dg[lane * (PB + 1) + j];
-          for (int k = j + 1; k <= lane; ++k) Dg[lane * (PB + 1) + k] -= lij * Dg[k * (PB + 1) + j];
-        }
-        __syncwarp();
+    // ---- blocked right-looking Cholesky, lower, in place in A ----
+    for (int p0 = 0; p0 < r; p0 += PB) {
+      const int b = min(PB, r - p0);
+      for (int e = t; e < b * b; e += kChol) {
+        int i = e % b, j = e / b;
+        Dg[i * (PB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
       }
-    }
-    __syncthreads();
-    for (int e = t; e < b * b; e += kChol) {
-      int i = e % b, j = e / b;
-      if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = Dg[i * (PB + 1) + j];
-    }
-    const int rows = r - p0 - b;
-    // panel: L[i, p0:p0+b] = A[i, p0:p0+b] * Dg^-T
-    for (int ii = t; ii < rows; ii += kChol) {
-      const int i = p0 + b + ii;
-      float a[PB];
-#pragma unroll
-      for (int c = 0; c < PB; ++c) a[c] = (c < b) ? A[i + (int64_t)r * (p0 + c)] : 0.f;
-#pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        if (c < b) {
-          float s = a[c];
-#pragma unroll
-          for (int k = 0; k < PB; ++k)
-            if (k < c) s -= a[k] * Dg[c * (PB + 1) + k];
-          a[c] = s / Dg[c * (PB + 1) + c];
+      __syncthreads();
+      if (warp == 0) {
+        for (int j = 0; j < b; ++j) {
+          float piv = Dg[j * (PB + 1) + j];
+          if (!(piv > floor)) {
+            if (lane == 0) bad = 1;
+            piv = floor;
+          }
+          piv = sqrtf(piv);
+          __syncwarp();
+          if (lane == j) Dg[j * (PB + 1) + j] = piv;
+          if (lane > j && lane < b) Dg[lane * (PB + 1) + j] /= piv;
+          __syncwarp();
+          if (lane > j && lane < b) {
+            float lij = Dg[lane * (PB + 1) + j];
+            for (int k = j + 1; k <= lane; ++k) Dg[lane * (PB + 1) + k] -= lij * Dg[k * (PB + 1) + j];
+          }
+          __syncwarp();
         }
       }
-#pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        if (c < b) A[i + (int64_t)r * (p0 + c)] = a[c];
-        Pn[ii * (PB + 1) + c] = (c < b) ? a[c] : 0.f;
+      __syncthreads();
+      for (int e = t; e < b * b; e += kChol) {
+        int i = e % b, j = e / b;
+        if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = Dg[i * (PB + 1) + j];
       }
-    }
-    __syncthreads();
-    // trailing update of the lower triangle, 8x8 tiles
-    const int nt = (rows + 7) / 8;
-    const int ntiles = nt * (nt + 1) / 2;
-    for (int tile = t; tile < ntiles; tile += kChol) {
-      // tile -> (bi >= bj)
-      int bi = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
-      while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-      while (bi * (bi + 1) / 2 > tile) --bi;
-      int bj = tile - bi * (bi + 1) / 2;
-      float acc[8][8];
+      const int rows = r - p0 - b;
+      // panel: L[i, p0:p0+b] = A[i, p0:p0+b] * Dg^-T
+      for (int ii = t; ii < rows; ii += kChol) {
+        const int i = p0 + b + ii;
+        float a[PB];
 #pragma unroll
-      for (int x = 0; x < 8; ++x)
+        for (int c = 0; c < PB; ++c) a[c] = (c < b) ? A[i + (int64_t)r * (p0 + c)] : 0.f;
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-      for (int c = 0; c < b; ++c) {
-        float u[8], v[8];
+        for (int c = 0; c < PB; ++c) {
+          if (c < b) {
+            float sacc = a[c];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-          int ri = bi * 8 + x, rj = bj * 8 + x;
-          u[x] = (ri < rows) ? Pn[ri * (PB + 1) + c] : 0.f;
-          v[x] = (rj < rows) ? Pn[rj * (PB + 1) + c] : 0.f;
+            for (int k = 0; k < PB; ++k)
+              if (k < c) sacc -= a[k] * Dg[c * (PB + 1) + k];
+            a[c] = sacc / Dg[c * (PB + 1) + c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+          if (c < b) A[i + (int64_t)r * (p0 + c)] = a[c];
+          Pn[ii * (PB + 1) + c] = (c < b) ? a[c] : 0.f;
+        }
+      }
+      __syncthreads();
+      // trailing update of the lower triangle, 8x8 tiles
+      const int nt = (rows + 7) / 8;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int tile = t; tile < ntiles; tile += kChol) {
+        int bi = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+        while (bi * (bi + 1) / 2 > tile) --bi;
+        int bj = tile - bi * (bi + 1) / 2;
+        float acc[8][8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+        for (int c = 0; c < b; ++c) {
+          float u[8], v[8];
+#pragma unroll
+          for (int x = 0; x < 8; ++x) {
+            int ri = bi * 8 + x, rj = bj * 8 + x;
+            u[x] = (ri < rows) ? Pn[ri * (PB + 1) + c] : 0.f;
+            v[x] = (rj < rows) ? Pn[rj * (PB + 1) + c] : 0.f;
+          }
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(u[x], v[y], acc[x][y]);
         }
 #pragma unroll
         for (int x = 0; x < 8; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(u[x], v[y], acc[x][y]);
-      }
-#pragma unroll
-      for (int x = 0; x < 8; ++x)
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-          int ri = bi * 8 + x, rj = bj * 8 + y;
-          if (ri < rows && rj < rows && ri >= rj) {
-            int64_t e = (p0 + b + ri) + (int64_t)r * (p0 + b + rj);
-            A[e] -= acc[x][y];
+          for (int y = 0; y < 8; ++y) {
+            int ri = bi * 8 + x, rj = bj * 8 + y;
+            if (ri < rows && rj < rows && ri >= rj) {
+              int64_t e = (p0 + b + ri) + (int64_t)r * (p0 + b + rj);
+              A[e] -= acc[x][y];
+            }
           }
-        }
+      }
+      __syncthreads();
     }
+    if (!bad) break;
+    if (t == 0 && flags) atomicOr(flags, 1);
+    rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
+    if (rel > 1e-2f) rel = 1e-2f;
     __syncthreads();
   }
 
   // ---- X = L^-1 (lower), blocked by 32 rows ----
   const int nb = (r + PB - 1) / PB;
   float* Di = Dg;                  // inverse of the current diagonal block, 32 x 33
-  float* Ls = Pn;                  // 32 x 33 tile of L
+  float* Ls = Pn;                  // 32 x 33 tile of L (diagonal block first)
   float* Xs = Pn + PB * (PB + 1);  // 32 x 33 tile of X
+  const int ti = t >> 5, tj = t & 31;   // 32 x 32 output element per thread
   for (int ib = 0; ib < nb; ++ib) {
     const int i0 = ib * PB, bi = min(PB, r - i0);
-    // inverse of the diagonal block, column `lane` per lane of warp 0
+    // stage the diagonal block of L (coalesced: lanes walk the rows)
+    Ls[tj * (PB + 1) + ti] = (tj < bi && ti < bi) ? A[(i0 + tj) + (int64_t)r * (i0 + ti)] : (tj == ti ? 1.f : 0.f);
+    __syncthreads();
+    // its inverse, column `lane` per lane of warp 0, in registers
     if (warp == 0) {
       float col[PB];
 #pragma unroll
-      for (int i = 0; i < PB; ++i) col[i] = 0.f;
-      if (lane < bi) {
-        for (int i = lane; i < bi; ++i) {
-          float s = (i == lane) ? 1.f : 0.f;
-          for (int k = lane; k < i; ++k) s -= A[(i0 + i) + (int64_t)r * (i0 + k)] * col[k];
-          col[i] = s / A[(i0 + i) + (int64_t)r * (i0 + i)];
-        }
+      for (int i = 0; i < PB; ++i) {
+        float sacc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) sacc -= Ls[i * (PB + 1) + k] * col[k];
+        col[i] = (i >= lane) ? sacc / Ls[i * (PB + 1) + i] : 0.f;
       }
 #pragma unroll
       for (int i = 0; i < PB; ++i) Di[i * (PB + 1) + lane] = (lane < bi && i < bi) ? col[i] : 0.f;
     }
     __syncthreads();
     // off-diagonal blocks X[ib, jb] = -Di * sum_{kb=jb}^{ib-1} L[ib,kb] X[kb,jb]
-    const int ti = t >> 5, tj = t & 31;   // 32 x 32 output element per thread
     for (int jb = 0; jb < ib; ++jb) {
       const int j0 = jb * PB;
-      float s = 0.f;
+      float sacc = 0.f;
       for (int kb = jb; kb < ib; ++kb) {
         const int k0 = kb * PB;
-        Ls[ti * (PB + 1) + tj] = (ti < bi) ? A[(i0 + ti) + (int64_t)r * (k0 + tj)] : 0.f;
-        Xs[ti * (PB + 1) + tj] = X[(k0 + ti) + (int64_t)r * (j0 + tj)];
+        // coalesced loads: consecutive lanes read consecutive rows
+        Ls[tj * (PB + 1) + ti] = (tj < bi) ? A[(i0 + tj) + (int64_t)r * (k0 + ti)] : 0.f;
+        Xs[tj * (PB + 1) + ti] = X[(k0 + tj) + (int64_t)r * (j0 + ti)];
         __syncthreads();
 #pragma unroll 8
-        for (int k = 0; k < PB; ++k) s += Ls[ti * (PB + 1) + k] * Xs[k * (PB + 1) + tj];
+        for (int k = 0; k < PB; ++k) sacc += Ls[ti * (PB + 1) + k] * Xs[k * (PB + 1) + tj];
         __syncthreads();
       }
-      Ls[ti * (PB + 1) + tj] = s;
+      Ls[ti * (PB + 1) + tj] = sacc;
       __syncthreads();
       float v = 0.f;
 #pragma unroll 8
       for (int k = 0; k < PB; ++k) v -= Di[ti * (PB + 1) + k] * Ls[k * (PB + 1) + tj];
-      if (ti < bi) X[(i0 + ti) + (int64_t)r * (j0 + tj)] = v;
+      Xs[ti * (PB + 1) + tj] = v;
+      __syncthreads();
+      // coalesced store of the block
+      if (tj < bi) X[(i0 + tj) + (int64_t)r * (j0 + ti)] = Xs[tj * (PB + 1) + ti];
       __syncthreads();
     }
     // diagonal block of X, zero above it
-    for (int e = t; e < PB * PB; e += kChol) {
-      int i = e / PB, j = e % PB;
-      if (i < bi && j < bi) X[(i0 + i) + (int64_t)r * (i0 + j)] = (i >= j) ? Di[i * (PB + 1) + j] : 0.f;
-    }
+    if (tj < bi && ti < bi) X[(i0 + tj) + (int64_t)r * (i0 + ti)] = (tj >= ti) ? Di[tj * (PB + 1) + ti] : 0.f;
     __syncthreads();
   }
   // Rinv(p, q) = Linv(q, p) / d_p for p <= q, 0 below the diagonal

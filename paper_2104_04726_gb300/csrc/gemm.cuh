@@ -24,6 +24,9 @@ struct Gemm {
   int64_t b_n = 0, b_k = 0, b_kh = 0, b_b = 0;
   float* C = nullptr;
   int64_t M_lo = 0, c_m = 0, c_mh = 0, N_lo = 0, c_n = 0, c_nh = 0, c_b = 0;
+  // optional second output (same values, another layout), strides as for C
+  float* C2 = nullptr;
+  int64_t c2_m = 0, c2_mh = 0, c2_n = 0, c2_nh = 0, c2_b = 0;
   float alpha = 1.f;
   bool accumulate = false;
   const int* skip = nullptr;      // device flag: when non-zero the launch is a no-op

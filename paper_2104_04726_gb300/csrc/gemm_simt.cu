@@ -155,6 +155,22 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
           float v = g.alpha * acc[i][j];
           *p = g.accumulate ? *p + v : v;
         }
+    if (g.C2) {
+      const int64_t M_lo2 = M_lo, N_lo2 = N_lo;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (!mok[i]) continue;
+        int64_t m = bm + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        int64_t mh = m / M_lo2, ml = m - mh * M_lo2;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (!nok[j]) continue;
+          int64_t n = bn + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+          int64_t nh = n / N_lo2, nl = n - nh * N_lo2;
+          g.C2[(int64_t)b * g.c2_b + ml * g.c2_m + mh * g.c2_mh + nl * g.c2_n + nh * g.c2_nh] = g.alpha * acc[i][j];
+        }
+      }
+    }
   }
 }
 

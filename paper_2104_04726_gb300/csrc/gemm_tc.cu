@@ -1,0 +1,525 @@
+// Tensor-core (tcgen05) GEMM for the large contractions of the Tucker-ALS
+// sweep: the mode products T x_n S^T (Eq. 8) and the factored Gram products.
+//
+// C(m, n) = alpha * sum_k A(m, k) B(n, k), both operands K-major, FP32
+// accumulation in tensor memory (TMEM).  One CTA computes a 128 x BN tile:
+//   warp 0    TMA producer: 128-byte-swizzled K slices of A and B into a
+//             STAGES-deep shared-memory ring (mbarrier full/empty pairs);
+//   warp 1    allocates BN TMEM columns; one thread issues tcgen05.mma
+//             (M=128, N=BN, K=32 bytes per instruction) and commits each
+//             stage back to its producer barrier;
+//   warps 2-5 epilogue: tcgen05.ld 32x32b of their 32 TMEM lanes, then the
+//             strided (two-level) store, accumulate or fused residual.
+// Kinds: kind::tf32 on FP32 data and kind::f16 on BF16 data.  Split-K over
+// grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
+// result is deterministic.  Every mbarrier wait is bounded (globaltimer,
+// 2 s); a timeout sets an error bit and the CTA tears down normally.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "gemm.cuh"
+#include "gemm_tc.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int kThreads = 192;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+struct TcArgs {
+  int64_t M, N;
+  int k_tiles_lo, k_tiles_total, kt_per_split, splits, batch;
+  float* C;
+  int64_t M_lo, c_m, c_mh, N_lo, c_n, c_nh, c_b;
+  float* C2;
+  int64_t c2_m, c2_mh, c2_n, c2_nh, c2_b;
+  float alpha;
+  int accumulate;
+  const float* ref;
+  double* partials;
+  float* split_ws;     // [split][batch][M][N] when splits > 1
+  const int* skip;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after kWaitNs without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile, 128-byte rows, 128-byte swizzle: 8-row atoms of
+// 1024 bytes (stride byte offset), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int KIND, int BN, int STAGES>
+struct Cfg {
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  // idesc: D=F32 (bits 4-5 = 1); A/B format (bits 7-9, 10-12): TF32 = 2,
+  // BF16 = 1; both K-major; N >> 3 at bit 17; M >> 4 at bit 24.
+  static constexpr uint32_t FMT = KIND == 0 ? 2u : 1u;
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+
+template <int KIND, int BN, int STAGES, bool RESID>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               const TcArgs args) {
+  using C = Cfg<KIND, BN, STAGES>;
+  if (args.skip && *args.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + STAGES * C::STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  __shared__ double red[4];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int b = (int)(blockIdx.z % args.batch);
+  const int split = (int)(blockIdx.z / args.batch);
+  const int kt_begin = split * args.kt_per_split;
+  int kt_end = kt_begin + args.kt_per_split;
+  if (kt_end > args.k_tiles_total) kt_end = args.k_tiles_total;
+  const int nkt = kt_end - kt_begin;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int i = 0; i < nkt; ++i) {
+      if (!mbar_wait(&empty[stage], phase ^ 1u)) {
+        ok = false;
+        break;
+      }
+      const int kt = kt_begin + i;
+      const int kh = kt / args.k_tiles_lo;
+      const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 0 ? 4 : 2));
+      uint8_t* sa = tiles + stage * C::STAGE;
+      mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
+      tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, b);
+      tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, b);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    if (!ok) atomicOr(args.err, 8);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int i = 0; i < nkt; ++i) {
+      if (!mbar_wait(&full[stage], phase)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(tiles + stage * C::STAGE);
+      const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + C::A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)   // 4 x 32 bytes of K per 128-byte row
+        mma<KIND>(tmem, da + 2 * kk, db + 2 * kk, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[stage]);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    mma_commit(accum);
+    if (!ok) atomicOr(args.err, 16);
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int wq = warp & 3;
+    const int64_t m = m0 + wq * 32 + lane;
+    const bool waited = mbar_wait(accum, 0);
+    if (!waited && lane == 0) atomicOr(args.err, 32);
+    tc_fence_after();
+    const bool mok = m < args.M;
+    const int64_t M_lo = args.M_lo, N_lo = args.N_lo;
+    const int64_t mh = m / M_lo, ml = m - mh * M_lo;
+    const int64_t moff = ml * args.c_m + mh * args.c_mh + (int64_t)b * args.c_b;
+    const int64_t moff2 = ml * args.c2_m + mh * args.c2_mh + (int64_t)b * args.c2_b;
+    double sq = 0.0;
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+      if (!waited || !mok) continue;
+      if (args.splits > 1) {
+        float* dst = args.split_ws + (((int64_t)split * args.batch + b) * args.M + m) * args.N;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t n = n0 + c0 + j;
+          if (n < args.N) dst[n] = __uint_as_float(v[j]);
+        }
+        continue;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t n = n0 + c0 + j;
+        if (n >= args.N) continue;
+        const int64_t nh = n / N_lo, nl = n - nh * N_lo;
+        const float val = args.alpha * __uint_as_float(v[j]);
+        if (RESID) {
+          const float d = __ldg(args.ref + moff + nl * args.c_n + nh * args.c_nh) - val;
+          sq += (double)d * (double)d;
+        } else {
+          float* p = args.C + moff + nl * args.c_n + nh * args.c_nh;
+          *p = args.accumulate ? *p + val : val;
+          if (args.C2) args.C2[moff2 + nl * args.c2_n + nh * args.c2_nh] = val;
+        }
+      }
+    }
+    if (RESID) {
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+      if (lane == 0) red[wq] = sq;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (wq == 0 && lane == 0) {
+        const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        args.partials[bid] = red[0] + red[1] + red[2] + red[3];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// Fixed-order reduction of split-K partial tiles into C (general strides).
+__global__ void split_reduce_kernel(const float* __restrict__ ws, TcArgs a) {
+  if (a.skip && *a.skip) return;
+  const int64_t total = (int64_t)a.batch * a.M * a.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int sp = 0; sp < a.splits; ++sp) s += ws[(int64_t)sp * total + e];
+    const int64_t n = e % a.N;
+    const int64_t bm = e / a.N;
+    const int64_t m = bm % a.M, b = bm / a.M;
+    const int64_t mh = m / a.M_lo, ml = m - mh * a.M_lo, nh = n / a.N_lo, nl = n - nh * a.N_lo;
+    const float val = a.alpha * s;
+    float* p = a.C + ml * a.c_m + mh * a.c_mh + nl * a.c_n + nh * a.c_nh + b * a.c_b;
+    *p = a.accumulate ? *p + val : val;
+    if (a.C2) a.C2[ml * a.c2_m + mh * a.c2_mh + nl * a.c2_n + nh * a.c2_nh + b * a.c2_b] = val;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+mes_status get_encode() {
+  if (g_encode) return MES_OK;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return mes::fail(MES_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return MES_OK;
+}
+
+// 4-D map {K_lo, rows, K_hi, batch} of a K-major operand.
+bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_t rows, int64_t K_hi,
+              int64_t batch, int64_t s_row, int64_t s_kh, int64_t s_b, int box_rows) {
+  const int E = kind == 0 ? 4 : 2;
+  cuuint64_t dims[4] = {(cuuint64_t)K_lo, (cuuint64_t)rows, (cuuint64_t)K_hi, (cuuint64_t)batch};
+  int64_t st[3] = {s_row * E, s_kh * E, s_b * E};
+  // unit dims get a harmless stride that keeps the strides increasing
+  if (K_hi == 1) st[1] = st[0] * rows;
+  if (batch == 1) st[2] = st[1] * (K_hi > 0 ? K_hi : 1);
+  for (int i = 0; i < 3; ++i)
+    if (st[i] <= 0 || st[i] % 16 != 0 || st[i] >= ((int64_t)1 << 40)) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+  cuuint64_t strides[3] = {(cuuint64_t)st[0], (cuuint64_t)st[1], (cuuint64_t)st[2]};
+  cuuint32_t box[4] = {(cuuint32_t)(128 / E), (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                        const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int BN, int STAGES>
+mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, dim3 grid, bool resid,
+                     cudaStream_t st) {
+  using C = Cfg<KIND, BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    MES_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, STAGES, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    MES_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN, STAGES, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr = true;
+  }
+  if (resid)
+    tc_gemm_kernel<KIND, BN, STAGES, true><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a);
+  else
+    tc_gemm_kernel<KIND, BN, STAGES, false><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+}  // namespace
+
+namespace mes {
+
+bool tc_eligible(const Gemm& g, int kind) {
+  const int E = kind == 0 ? 4 : 2;
+  if (g.a_k != 1 || g.b_k != 1) return false;
+  if ((g.a_m * E) % 16 || (g.b_n * E) % 16) return false;
+  if (g.K_hi > 1 && ((g.a_kh * E) % 16 || (g.b_kh * E) % 16)) return false;
+  if (g.batch > 1 && (((g.a_b * E) % 16) || ((g.b_b * E) % 16))) return false;
+  if (reinterpret_cast<uintptr_t>(g.A) % 16 || reinterpret_cast<uintptr_t>(g.B) % 16) return false;
+  if (g.M > INT32_MAX || g.N > INT32_MAX || g.K_lo > INT32_MAX) return false;
+  return true;
+}
+
+mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_elems, int* err, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return MES_OK;
+  MES_TRY(get_encode());
+  if (!tc_eligible(g, kind)) return fail(MES_ERR_INVALID_ARG, "gemm_tc: operands not TMA/K-major eligible");
+  const int BK = 128 / (kind == 0 ? 4 : 2);
+  const int bn = g.N > 128 ? 256 : 128;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, g.batch, g.a_m, g.a_kh, g.a_b, BM) ||
+      !make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, g.batch, g.b_n, g.b_kh, g.b_b, bn))
+    return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map rejected");
+  TcArgs a;
+  a.M = g.M;
+  a.N = g.N;
+  a.k_tiles_lo = (int)((g.K_lo + BK - 1) / BK);
+  a.k_tiles_total = a.k_tiles_lo * (int)g.K_hi;
+  a.batch = g.batch;
+  a.C = g.C;
+  a.M_lo = g.M_lo > 0 ? g.M_lo : g.M;
+  a.c_m = g.c_m; a.c_mh = g.c_mh;
+  a.N_lo = g.N_lo > 0 ? g.N_lo : g.N;
+  a.c_n = g.c_n; a.c_nh = g.c_nh; a.c_b = g.c_b;
+  a.C2 = g.C2;
+  a.c2_m = g.c2_m; a.c2_mh = g.c2_mh; a.c2_n = g.c2_n; a.c2_nh = g.c2_nh; a.c2_b = g.c2_b;
+  a.alpha = g.alpha;
+  a.accumulate = g.accumulate ? 1 : 0;
+  a.ref = g.ref;
+  a.partials = g.partials;
+  a.skip = g.skip;
+  a.err = err;
+  // split K when the tile grid leaves most SMs idle
+  const int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + bn - 1) / bn) * g.batch;
+  int splits = 1;
+  const int64_t sms = sm_count();
+  if (!g.ref && split_ws) {
+    while (tiles * splits * 2 <= sms && a.k_tiles_total / (splits * 2) >= 4 &&
+           (int64_t)(splits * 2) * g.batch * g.M * g.N <= split_ws_elems)
+      splits *= 2;
+  }
+  a.kt_per_split = (a.k_tiles_total + splits - 1) / splits;
+  splits = (a.k_tiles_total + a.kt_per_split - 1) / a.kt_per_split;
+  if (splits < 1) splits = 1;
+  a.splits = splits;
+  a.split_ws = split_ws;
+  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + bn - 1) / bn), (unsigned)(g.batch * splits));
+  {
+    ProfScope prof(kind == 0 ? "gemm_tf32_tc" : "gemm_bf16_tc", st,
+                   2.0 * g.M * g.N * (double)g.K_lo * g.K_hi * g.batch,
+                   (kind == 0 ? 4.0 : 2.0) * g.batch * ((double)g.M + g.N) * g.K_lo * g.K_hi +
+                       4.0 * g.batch * g.M * (double)g.N);
+    if (kind == 0) {
+      if (bn == 256) MES_TRY((launch_tc<0, 256, 4>(ma, mb, a, grid, g.ref != nullptr, st)));
+      else MES_TRY((launch_tc<0, 128, 6>(ma, mb, a, grid, g.ref != nullptr, st)));
+    } else {
+      if (bn == 256) MES_TRY((launch_tc<1, 256, 4>(ma, mb, a, grid, g.ref != nullptr, st)));
+      else MES_TRY((launch_tc<1, 128, 6>(ma, mb, a, grid, g.ref != nullptr, st)));
+    }
+  }
+  if (splits > 1) {
+    ProfScope prof("split_reduce", st, 0.0, 4.0 * splits * g.batch * g.M * (double)g.N);
+    const int64_t total = (int64_t)g.batch * g.M * g.N;
+    split_reduce_kernel<<<grid_for(total, 256, sms * 8), 256, 0, st>>>(split_ws, a);
+    MES_LAUNCH_CHECK();
+  }
+  return MES_OK;
+}
+
+}  // namespace mes
+
+namespace {
+
+__global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16_raw* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // round to nearest even on the upper 16 bits
+    uint32_t u = __float_as_uint(in[i]);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    __nv_bfloat16_raw r;
+    r.x = (unsigned short)(u >> 16);
+    out[i] = r;
+  }
+}
+
+}  // namespace
+
+// Test hook: C[m*N + n] = sum_k A[m*K + k] * B[n*K + k] (both row-major,
+// K-major), through the CUDA-core kernel (impl 0), kind::tf32 (impl 1) or
+// kind::f16 on BF16-rounded inputs (impl 2).
+extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M,
+                                        int64_t N, int64_t K, int batch, void* stream) {
+  mes::clear_error();
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 2)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_gemm_selftest: bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::AuditScope audit_scope;
+  mes::audit_register(A, (size_t)(batch * M * K) * 4);
+  mes::audit_register(B, (size_t)(batch * N * K) * 4);
+  mes::audit_register(C, (size_t)(batch * M * N) * 4);
+  mes::Scratch scr(st);
+  mes::Gemm g;
+  g.M = M; g.N = N; g.K_lo = K; g.batch = batch;
+  g.A = A; g.a_m = K; g.a_k = 1; g.a_b = M * K;
+  g.B = B; g.b_n = K; g.b_k = 1; g.b_b = N * K;
+  g.C = C; g.c_m = N; g.c_n = 1; g.c_b = M * N;
+  if (impl == 0) return mes::gemm_f32(g, st);
+  int* err = nullptr;
+  float* ws = nullptr;
+  const int64_t ws_elems = 64 * batch * M * N;
+  MES_TRY(scr.alloc(&err, 1));
+  MES_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  MES_TRY(scr.alloc(&ws, ws_elems));
+  if (impl == 2) {
+    __nv_bfloat16_raw *Ab, *Bb;
+    MES_TRY(scr.alloc(&Ab, batch * M * K));
+    MES_TRY(scr.alloc(&Bb, batch * N * K));
+    to_bf16_kernel<<<mes::grid_for(batch * M * K, 256, 4096), 256, 0, st>>>(A, Ab, batch * M * K);
+    to_bf16_kernel<<<mes::grid_for(batch * N * K, 256, 4096), 256, 0, st>>>(B, Bb, batch * N * K);
+    MES_LAUNCH_CHECK();
+    g.A = reinterpret_cast<const float*>(Ab);
+    g.B = reinterpret_cast<const float*>(Bb);
+  }
+  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : 1, ws, ws_elems, err, st));
+  int herr = 0;
+  MES_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MES_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr) return mes::fail(MES_ERR_TIMEOUT, "mes_gemm_selftest: pipeline wait gave up (flags %d)", herr);
+  return MES_OK;
+}

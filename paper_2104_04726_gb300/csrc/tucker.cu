@@ -33,6 +33,8 @@
 // no-ops, so the host enqueues max_iters sweeps without reading anything back.
 // The returned fit is recomputed from the explicit residual ||T - T_hat||,
 // which does not suffer the cancellation of ||T||^2 - ||Q||^2 in FP32.
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "gemm.cuh"
@@ -44,8 +46,10 @@ using mes::Gemm;
 using mes::Fibres;
 using mes::KronDesc;
 
-constexpr float kShiftZ = 1e-7f;   // relative shift of the Z-preconditioning Cholesky
-constexpr float kShiftW = 1e-6f;   // relative shift of the first CholeskyQR pass
+// Starting relative shifts of the Z-preconditioning Cholesky and of the
+// first CholeskyQR pass (the Cholesky kernel raises them on breakdown).
+static float kShiftZ = 1e-5f;
+static float kShiftW = 1e-5f;
 
 struct Shape {
   int N = 0;
@@ -268,6 +272,8 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: negative iteration option");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (getenv("MES_SHIFT_Z")) kShiftZ = (float)atof(getenv("MES_SHIFT_Z"));
+  if (getenv("MES_SHIFT_W")) kShiftW = (float)atof(getenv("MES_SHIFT_W"));
   mes::AuditScope audit_scope;
   {
     int64_t nX = 1, nQ = 1;
@@ -574,6 +580,12 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
     }
   }
 
+  if (getenv("MES_DEBUG")) {
+    int hf[2] = {0, 0};
+    cudaMemcpyAsync(hf, done, sizeof(hf), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    fprintf(stderr, "[mes] done=%d numerics_flags=%d\n", hf[0], hf[1]);
+  }
   // ---- fit from the explicit residual ----
   if (fit) {
     const float* fac[8];

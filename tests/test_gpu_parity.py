@@ -347,6 +347,9 @@ def test_fhd_full_size_properties(mes):
         want = tucker.element(core, Us, idx)
         got = float(Xhn[idx[::-1]])
         assert abs(got - want) < 2e-5, (idx, got, want)
+    # energy identity ||T||^2 - ||Q||^2 = ||T - T_hat||^2: with an FP32 core
+    # ||Q||^2 carries ~sqrt(s_1) * 2^-24 relative error of ||T||^2 (~3e-6
+    # here), which is most of the residual at fit ~0.998
     lhs = np.sum(T ** 2) - np.sum(core ** 2)
     rhs = np.sum((T - Xr) ** 2)
-    assert abs(lhs - rhs) < 0.05 * rhs
+    assert abs(lhs - rhs) < 3e-6 * np.sum(T ** 2)
