@@ -168,9 +168,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mes", choices=["mes", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--stacks", type=int, default=8, help="independent stacks per step, one CUDA stream each")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -203,54 +204,87 @@ def main():
     dims = [spec.s1, spec.s2, 3, spec.K]
     ranks = list(cfg["ranks"])
     iters = cfg["iters"]
-    img = synth.make_stack(spec, synth.seed_for(name, rank))
-    rgb_host = torch.from_numpy(img).pin_memory()
-    rgb = rgb_host.to(dev)
+    S = args.stacks
+    P = 1
+    for r in ranks[2:]:
+        P *= r
 
-    # device-resident outputs reused by every step
-    X = torch.empty(torch.Size([spec.K, 3, spec.s2, spec.s1]), dtype=torch.float32, device=dev)
-    n2 = torch.empty((), dtype=torch.float64, device=dev)
-    core = torch.empty(mes.torch_shape(ranks), dtype=torch.float32, device=dev)
-    facs = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
-    fit = torch.empty((), dtype=torch.float64, device=dev)
-    itd = torch.zeros((), dtype=torch.int32, device=dev)
-    outs = (core, facs, fit, itd, None)
+    class Stack:
+        """Device-resident inputs and outputs of one stack, and its stream."""
 
-    def step():
-        mes.colour_convert(rgb, cfg["space"], out=X, norm2=n2)
-        mes.tucker_als(X, dims, ranks, max_iters=iters, tol=0.0, precision=args.precision, outputs=outs)
-        q, sc = mes.quantize_core(core, ranks, 16)
-        Xh, sse = mes.reconstruct(core, facs, dims, ranks, ref=X)
-        return q, sc, sse
+        def __init__(self, idx):
+            img = synth.make_stack(spec, synth.seed_for(name, rank * S + idx))
+            self.rgb_host = torch.from_numpy(img).pin_memory()
+            self.rgb = self.rgb_host.to(dev)
+            self.X = torch.empty((spec.K, 3, spec.s2, spec.s1), dtype=torch.float32, device=dev)
+            self.n2 = torch.empty((), dtype=torch.float64, device=dev)
+            self.core = torch.empty(mes.torch_shape(ranks), dtype=torch.float32, device=dev)
+            self.facs = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
+            self.fit = torch.empty((), dtype=torch.float64, device=dev)
+            self.itd = torch.zeros((), dtype=torch.int32, device=dev)
+            self.stream = torch.cuda.Stream(device=dev)
+            self.q_host = torch.empty(mes.torch_shape(ranks), dtype=torch.int16, pin_memory=True)
+            self.s_host = torch.empty((P,), dtype=torch.float32, pin_memory=True)
+            self.f_host = [torch.empty((r, s), dtype=torch.float32, pin_memory=True) for s, r in zip(dims, ranks)]
+            self.fit_host = torch.empty((), dtype=torch.float64, pin_memory=True)
 
-    stream = torch.cuda.current_stream()
+        def run(self, e2e=False):
+            with torch.cuda.stream(self.stream):
+                if e2e:
+                    self.rgb.copy_(self.rgb_host, non_blocking=True)
+                mes.colour_convert(self.rgb, cfg["space"], out=self.X, norm2=self.n2)
+                mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=args.precision,
+                               outputs=(self.core, self.facs, self.fit, self.itd, None))
+                q, sc = mes.quantize_core(self.core, ranks, 16)
+                mes.reconstruct(self.core, self.facs, dims, ranks, ref=self.X)
+                if e2e:
+                    self.q_host.copy_(q, non_blocking=True)
+                    self.s_host.copy_(sc, non_blocking=True)
+                    for a, b in zip(self.f_host, self.facs):
+                        a.copy_(b, non_blocking=True)
+                    self.fit_host.copy_(self.fit, non_blocking=True)
+
+    stacks = [Stack(i) for i in range(S)]
+    main = torch.cuda.current_stream()
+
+    def step(e2e=False):
+        start = torch.cuda.Event()
+        start.record(main)
+        for st_ in stacks:
+            st_.stream.wait_event(start)
+            st_.run(e2e)
+        for st_ in stacks:
+            main.wait_stream(st_.stream)
+
+    def timed(n, e2e=False):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for _ in range(n):
+            step(e2e)
+        b.record(main)
+        torch.cuda.synchronize()
+        t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, device events, barrier + sync on both sides
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # ---- timed region: K steps of S stacks, device events, barrier + sync
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_max = timed(args.steps)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    stacks = args.steps * world
-    value = stacks / (ms_max / 1e3)
+    n_stacks = args.steps * S * world
+    value = n_stacks / (ms_max / 1e3)
 
-    # ---- per-kernel profile over the same K steps (events on the launch stream)
+    # ---- per-kernel profile over K more steps (events on each launch stream)
     lib.mes_profile_enable(1)
     for _ in range(args.steps):
         step()
@@ -267,13 +301,22 @@ def main():
     lib.mes_profile_enable(0)
     fams.sort(key=lambda f: -f["ms"])
     total_ms = sum(f["ms"] for f in fams) or 1.0
-    launches = sum(f["launches"] for f in fams) // max(args.steps, 1) * args.steps
+    launches = sum(f["launches"] for f in fams)
 
     peaks, peak_src = _peaks()
     top = fams[0]
-    if top["name"].startswith("gemm_f32") or top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
-        # FP32 CUDA-core GEMM: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if top["name"].startswith("gemm_tf32_tc") or top["name"].startswith("gemm_bf16_tc"):
+        # tensor-core product: TF32 peak = half the measured BF16 dense peak
+        # (nominal TF32:BF16 ratio 1:2); sustained figure (timed inside a long step)
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if "tf32" in top["name"] else 1.0)
+        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained x {'0.5 (tf32)' if 'tf32' in top['name'] else '1'}",
+                "share": top["ms"] / total_ms}
+    elif top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
+        # CUDA-core FP32 arithmetic: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
         peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -287,48 +330,22 @@ def main():
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "share": top["ms"] / total_ms}
 
     # ---- end to end through the public API with host buffers
-    q_host = torch.empty(mes.torch_shape(ranks), dtype=torch.int16, pin_memory=True)
-    P = 1
-    for r in ranks[2:]:
-        P *= r
-    s_host = torch.empty((P,), dtype=torch.float32, pin_memory=True)
-    f_host = [torch.empty((r, s), dtype=torch.float32, pin_memory=True) for s, r in zip(dims, ranks)]
-    fit_host = torch.empty((), dtype=torch.float64, pin_memory=True)
-    h2d = rgb_host.numel()
-    d2h = q_host.numel() * 2 + P * 4 + sum(f.numel() * 4 for f in f_host) + 8
-
-    def e2e_step():
-        rgb.copy_(rgb_host, non_blocking=True)
-        q, sc, _ = step()
-        q_host.copy_(q, non_blocking=True)
-        s_host.copy_(sc, non_blocking=True)
-        for a, b in zip(f_host, facs):
-            a.copy_(b, non_blocking=True)
-        fit_host.copy_(fit, non_blocking=True)
-
-    e2e_step()
+    h2d = S * stacks[0].rgb_host.numel()
+    d2h = S * (stacks[0].q_host.numel() * 2 + P * 4 + sum(f.numel() * 4 for f in stacks[0].f_host) + 8)
+    step(True)
     torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    e2 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    e2[0].record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e2[1].record(stream)
-    torch.cuda.synchronize()
-    t2 = torch.tensor([e2[0].elapsed_time(e2[1])], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-    e2e_val = stacks / (float(t2.item()) / 1e3)
-
+    e2e_ms = timed(args.steps, e2e=True)
+    e2e_val = n_stacks / (e2e_ms / 1e3)
+    fit = stacks[0].fit
+    ms_per_step = ms_max / args.steps
     fit_val = float(fit.item())
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "stacks/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
                 "data": "synthetic",
                 "config": {"workload": name, "dims": dims, "ranks": ranks, "sweeps": iters, "colour": cfg["space"],
-                           "precision": args.precision, "quant_bits": 16,
+                           "precision": args.precision, "quant_bits": 16, "stacks_per_step": S,
                            "l2": "inputs larger than L2 (stack 249 MB FP32 + second layout 249 MB per step)",
                            "parallelism": f"stack-parallel x{world}"},
                 "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,

@@ -55,7 +55,7 @@ typedef enum mes_colour {
 typedef enum mes_precision {
   MES_PREC_FP32 = 0,  /* every contraction in FP32 (CUDA cores)            */
   MES_PREC_BF16 = 1,  /* tensor-core BF16 inputs, FP32 accumulation        */
-  MES_PREC_BF16X3 = 2 /* split-BF16 (hi+lo, three products), FP32 accum.   */
+  MES_PREC_TF32 = 2   /* tensor-core TF32 inputs (FP32 data), FP32 accum.  */
 } mes_precision;
 
 /* Thread-local text of the last error on this thread ("" if none). */
@@ -91,7 +91,9 @@ mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_t s2, int64
  * options pointer means all defaults.  Fields equal to 0 take the default.
  */
 typedef struct mes_als_opts {
-  int precision;        /* mes_precision of the large contractions (FP32)     */
+  int precision;        /* mes_precision of the large contractions (FP32).
+                           The Gram and orthonormalisation products of the
+                           factor update stay FP32 in every form.           */
   int init_iters;       /* subspace steps of the T-HOSVD initialisation (4)   */
   int inner_iters;      /* subspace steps per factor update in a sweep (2)    */
   uint64_t seed;        /* seed of the random start block of the init (1)     */

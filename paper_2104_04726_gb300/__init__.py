@@ -22,7 +22,7 @@ __all__ = ["colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequ
            "version", "torch_shape", "paper_dims", "PRECISIONS", "SPACES", "MesError"]
 
 MesError = _lib.MesError
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2}
 SPACES = {"ycbcr": 0, "ipt": 1}
 
 

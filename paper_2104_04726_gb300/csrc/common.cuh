@@ -4,10 +4,35 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 
 #include "mes.h"
 
 namespace mes {
+
+// Round to the nearest TF32 value (10 explicit mantissa bits), ties to even.
+// The tcgen05 kind::tf32 product reads FP32 operands and ignores their 13 low
+// mantissa bits, i.e. truncates; operands stored pre-rounded with this
+// function make its input rounding unbiased.  Inf and NaN pass unchanged.
+__host__ __device__ __forceinline__ float round_tf32(float x) {
+#ifdef __CUDA_ARCH__
+  unsigned u = __float_as_uint(x);
+#else
+  unsigned u;
+  memcpy(&u, &x, 4);
+#endif
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+  }
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float y;
+  memcpy(&y, &u, 4);
+  return y;
+#endif
+}
 
 // Records a formatted message in the thread-local error buffer and returns s.
 mes_status fail(mes_status s, const char* fmt, ...);

@@ -1,13 +1,9 @@
 // Small dense solvers of the factor update (Section III-B, text after Eq. 8:
 // the factor is taken from the leading eigenvectors of the Gram).
 //
-//  * cholinv:   equilibrated, optionally shifted Cholesky of an r x r Gram
-//               M = W^T W and the inverse of its factor, giving Rinv with
-//               W * Rinv orthonormal (one pass of shifted CholeskyQR).  One
-//               CTA of 1024 threads, FP32, blocked by 32 columns: the
-//               diagonal block is factored by one warp in shared memory, the
-//               panel below by one row per thread, the trailing update by
-//               8x8 register tiles; the inverse is blocked the same way.
+//  * chol + trsm: one pass of shifted CholeskyQR, V = W R^-1 with
+//               R^T R = M = W^T W (equilibrated, shifted): the Cholesky on
+//               one CTA, the triangular solve over all rows of W on many.
 //  * eig_small: FP64 cyclic Jacobi for the Grams of the small modes
 //               (colour, view x exposure; n <= 32), one warp per matrix.
 //  * eig_mid:   FP32 parallel (round-robin) Jacobi for an r x r symmetric
@@ -21,43 +17,76 @@
 
 namespace {
 
-constexpr int kChol = 1024;
 constexpr int PB = 32;
 
 // --------------------------------------------------------------------------
-// cholinv
+// chol: equilibrated, shifted Cholesky of a symmetric r x r Gram M (one CTA,
+// 512 threads).  A = D^-1 M D^-1 + shift * r * I = L L^T with D = diag(M)^1/2.
+// Outputs L (lower triangle of `L`, column-major) and dinv = 1 / diag(D).
+// Blocked by 32 columns: the diagonal block is factored by one warp in
+// registers, the panel below is solved by forward substitution (one row per
+// thread), the trailing lower triangle is updated in 8 x 8 tiles.
+// The shift starts at shift_rel and is raised tenfold (up to 1e-2) whenever a
+// pivot falls below max(1e-7, 0.1 * shift): it must dominate the FP32
+// rounding of the Gram, yet stay small so the next pass is well conditioned.
 // --------------------------------------------------------------------------
+constexpr int kChol = 512;
+
+__device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad) {
+  const int lane = threadIdx.x & 31;
+  float row[PB];
+#pragma unroll
+  for (int k = 0; k < PB; ++k) row[k] = (k <= lane && lane < b && k < b) ? Dg[lane * (PB + 1) + k] : (k == lane ? 1.f : 0.f);
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    float piv = __shfl_sync(0xffffffffu, row[j], j);
+    if (j < b) {
+      if (!(piv > floor)) {
+        if (lane == 0) *bad = 1;
+        piv = floor;
+      }
+    } else {
+      piv = 1.f;
+    }
+    piv = sqrtf(piv);
+    if (lane == j) row[j] = piv;
+    else if (lane > j) row[j] /= piv;
+    const float lij = row[j];
+#pragma unroll
+    for (int k = j + 1; k < PB; ++k) {
+      const float lkj = __shfl_sync(0xffffffffu, row[j], k);
+      if (lane >= k) row[k] -= lij * lkj;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PB; ++k) Dg[lane * (PB + 1) + k] = (k <= lane) ? row[k] : 0.f;
+}
+
 __global__ void __launch_bounds__(kChol)
-cholinv_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ A,
-               float* __restrict__ X, float* __restrict__ Rinv, int* __restrict__ flags,
-               const int* __restrict__ skip) {
+chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ A,
+            float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip) {
   if (skip && *skip) return;
   extern __shared__ float smem[];
-  float* dinv = smem;                       // r
+  float* dinv = smem;                       // 1024
   float* Dg = dinv + 1024;                  // 32 x 33
-  float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel) / reuse
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
+  __shared__ int bad;
+  const int t = threadIdx.x, warp = t >> 5;
 
-  // equilibration d_i = sqrt(M_ii)
   for (int i = t; i < r; i += kChol) {
     float v = Min[i + (int64_t)r * i];
-    float d = (v > 0.f && isfinite(v)) ? sqrtf(v) : 1.f;
-    if (!(v > 0.f && isfinite(v)) && flags) atomicOr(flags, 2);
-    dinv[i] = 1.f / d;
+    bool ok = v > 0.f && isfinite(v);
+    if (!ok && flags) atomicOr(flags, 2);
+    float dv = 1.f / (ok ? sqrtf(v) : 1.f);
+    dinv[i] = dv;
+    dinv_out[i] = dv;
   }
   __syncthreads();
-  // Shifted Cholesky with restarts: the shift must dominate the FP32
-  // rounding of the Gram (else a pivot goes non-positive) yet stay small (the
-  // next unshifted pass needs W * Rinv well conditioned).  Start at
-  // shift_rel and, when a pivot falls below the floor, restart with a ten
-  // times larger relative shift (at most 1e-2).
-  __shared__ int bad;
   float rel = shift_rel;
   for (int attempt = 0; attempt < 8; ++attempt) {
     const float shift = rel * (float)r;
     const float floor = fmaxf(1e-7f, 0.1f * shift);
     if (t == 0) bad = 0;
-    // A = D^-1 M D^-1 + shift I  (lower triangle, column-major)
     for (int64_t e = t; e < (int64_t)r * r; e += kChol) {
       int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
       if (i >= j) {
@@ -67,41 +96,21 @@ cholinv_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __r
       }
     }
     __syncthreads();
-
-    // ---- blocked right-looking Cholesky, lower, in place in A ----
     for (int p0 = 0; p0 < r; p0 += PB) {
       const int b = min(PB, r - p0);
-      for (int e = t; e < b * b; e += kChol) {
-        int i = e % b, j = e / b;
-        Dg[i * (PB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
+      for (int e = t; e < PB * PB; e += kChol) {
+        int i = e & 31, j = e >> 5;
+        Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
       }
       __syncthreads();
-      if (warp == 0) {
-        for (int j = 0; j < b; ++j) {
-          float piv = Dg[j * (PB + 1) + j];
-          if (!(piv > floor)) {
-            if (lane == 0) bad = 1;
-            piv = floor;
-          }
-          piv = sqrtf(piv);
-          __syncwarp();
-          if (lane == j) Dg[j * (PB + 1) + j] = piv;
-          if (lane > j && lane < b) Dg[lane * (PB + 1) + j] /= piv;
-          __syncwarp();
-          if (lane > j && lane < b) {
-            float lij = Dg[lane * (PB + 1) + j];
-            for (int k = j + 1; k <= lane; ++k) Dg[lane * (PB + 1) + k] -= lij * Dg[k * (PB + 1) + j];
-          }
-          __syncwarp();
-        }
-      }
+      if (warp == 0) warp_chol32(Dg, b, floor, &bad);
       __syncthreads();
       for (int e = t; e < b * b; e += kChol) {
         int i = e % b, j = e / b;
         if (i >= j) A[(p0 + i) + (int64_t)r * (p0 + j)] = Dg[i * (PB + 1) + j];
       }
       const int rows = r - p0 - b;
-      // panel: L[i, p0:p0+b] = A[i, p0:p0+b] * Dg^-T
+      // panel: L[i, p0:p0+b] solves x L_pp^T = A[i, p0:p0+b] (forward substitution)
       for (int ii = t; ii < rows; ii += kChol) {
         const int i = p0 + b + ii;
         float a[PB];
@@ -109,22 +118,18 @@ cholinv_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __r
         for (int c = 0; c < PB; ++c) a[c] = (c < b) ? A[i + (int64_t)r * (p0 + c)] : 0.f;
 #pragma unroll
         for (int c = 0; c < PB; ++c) {
-          if (c < b) {
-            float sacc = a[c];
+          float v = a[c];
 #pragma unroll
-            for (int k = 0; k < PB; ++k)
-              if (k < c) sacc -= a[k] * Dg[c * (PB + 1) + k];
-            a[c] = sacc / Dg[c * (PB + 1) + c];
-          }
+          for (int k = 0; k < c; ++k) v = fmaf(-a[k], Dg[c * (PB + 1) + k], v);
+          a[c] = (c < b) ? v / Dg[c * (PB + 1) + c] : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < PB; ++c) {
           if (c < b) A[i + (int64_t)r * (p0 + c)] = a[c];
-          Pn[ii * (PB + 1) + c] = (c < b) ? a[c] : 0.f;
+          Pn[ii * (PB + 1) + c] = a[c];
         }
       }
       __syncthreads();
-      // trailing update of the lower triangle, 8x8 tiles
       const int nt = (rows + 7) / 8;
       const int ntiles = nt * (nt + 1) / 2;
       for (int tile = t; tile < ntiles; tile += kChol) {
@@ -169,65 +174,122 @@ cholinv_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __r
     if (rel > 1e-2f) rel = 1e-2f;
     __syncthreads();
   }
+}
 
-  // ---- X = L^-1 (lower), blocked by 32 rows ----
+// --------------------------------------------------------------------------
+// trsm: V = W D^-1 L^-T for an s x r column-major W (rows independent), i.e.
+// W * Rinv with Rinv = D^-1 L^-T, without forming Rinv.  ROWS rows per CTA
+// live in shared memory; column blocks of 32 in order:
+//   1. subtract the solved blocks times L: a ROWS x 32 x c0 product, 4 x 4
+//      register tiles, L staged in 32 x 32 tiles (next tile prefetched into
+//      registers while the current one is used);
+//   2. forward substitution with the 32 x 32 diagonal block of L, one row
+//      per thread.
+// With `round`, V is stored rounded to TF32 (an operand of kind::tf32).
+// --------------------------------------------------------------------------
+constexpr int kTrsm = 256;
+
+template <int ROWS>
+__global__ void __launch_bounds__(kTrsm)
+trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restrict__ L,
+            const float* __restrict__ dinv, float* __restrict__ V, int round, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ float sm[];
+  const int ld = r + 1;
+  float* Vs = sm;                    // ROWS x ld
+  float* Lt = Vs + ROWS * ld;        // 32 x 33
+  const int t = threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
+  for (int e = t; e < ROWS * r; e += kTrsm) {
+    int i = e % ROWS, c = e / ROWS;
+    int64_t row = row0 + i;
+    Vs[i * ld + c] = (row < s) ? W[row + s * c] * dinv[c] : 0.f;
+  }
+  __syncthreads();
+  constexpr int TR = ROWS / 32;       // rows per thread in the update (4 x ... tiles)
+  const int ty = t >> 3, tx = t & 7;  // 32 row groups x 8 column groups of 4
   const int nb = (r + PB - 1) / PB;
-  float* Di = Dg;                  // inverse of the current diagonal block, 32 x 33
-  float* Ls = Pn;                  // 32 x 33 tile of L (diagonal block first)
-  float* Xs = Pn + PB * (PB + 1);  // 32 x 33 tile of X
-  const int ti = t >> 5, tj = t & 31;   // 32 x 32 output element per thread
-  for (int ib = 0; ib < nb; ++ib) {
-    const int i0 = ib * PB, bi = min(PB, r - i0);
-    // stage the diagonal block of L (coalesced: lanes walk the rows)
-    Ls[tj * (PB + 1) + ti] = (tj < bi && ti < bi) ? A[(i0 + tj) + (int64_t)r * (i0 + ti)] : (tj == ti ? 1.f : 0.f);
-    __syncthreads();
-    // its inverse, column `lane` per lane of warp 0, in registers
-    if (warp == 0) {
-      float col[PB];
+  for (int cb = 0; cb < nb; ++cb) {
+    const int c0 = cb * PB;
+    if (c0 > 0) {
+      float acc[TR][4];
 #pragma unroll
-      for (int i = 0; i < PB; ++i) {
-        float sacc = (i == lane) ? 1.f : 0.f;
+      for (int a = 0; a < TR; ++a)
 #pragma unroll
-        for (int k = 0; k < i; ++k) sacc -= Ls[i * (PB + 1) + k] * col[k];
-        col[i] = (i >= lane) ? sacc / Ls[i * (PB + 1) + i] : 0.f;
+        for (int j = 0; j < 4; ++j) acc[a][j] = 0.f;
+      // prefetch the first L tile: Lt[c][kk] = L[(c0 + c) + r (k0 + kk)]
+      float pre[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int e = t + q * kTrsm, c = e & 31, kk = e >> 5;
+        pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * kk] : 0.f;
+      }
+      for (int k0 = 0; k0 < c0; k0 += PB) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int e = t + q * kTrsm, c = e & 31, kk = e >> 5;
+          Lt[c * (PB + 1) + kk] = pre[q];
+        }
+        __syncthreads();
+        if (k0 + PB < c0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int e = t + q * kTrsm, c = e & 31, kk = e >> 5;
+            pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * (k0 + PB + kk)] : 0.f;
+          }
+        }
+#pragma unroll 4
+        for (int kk = 0; kk < PB; ++kk) {
+          float a[TR], bq[4];
+#pragma unroll
+          for (int x = 0; x < TR; ++x) a[x] = Vs[(ty + 32 * x) * ld + k0 + kk];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bq[j] = Lt[(tx * 4 + j) * (PB + 1) + kk];
+#pragma unroll
+          for (int x = 0; x < TR; ++x)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[x][j] = fmaf(a[x], bq[j], acc[x][j]);
+        }
+        __syncthreads();
       }
 #pragma unroll
-      for (int i = 0; i < PB; ++i) Di[i * (PB + 1) + lane] = (lane < bi && i < bi) ? col[i] : 0.f;
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int c = tx * 4 + j;
+          if (c0 + c < r) Vs[(ty + 32 * x) * ld + c0 + c] -= acc[x][j];
+        }
+    }
+    // diagonal block of L into Lt (Lt[c][k] = L[c0 + c][c0 + k])
+    for (int e = t; e < PB * PB; e += kTrsm) {
+      int c = e & 31, k = e >> 5;
+      Lt[c * (PB + 1) + k] = (c0 + c < r && c0 + k < r) ? L[(c0 + c) + (int64_t)r * (c0 + k)] : (c == k ? 1.f : 0.f);
     }
     __syncthreads();
-    // off-diagonal blocks X[ib, jb] = -Di * sum_{kb=jb}^{ib-1} L[ib,kb] X[kb,jb]
-    for (int jb = 0; jb < ib; ++jb) {
-      const int j0 = jb * PB;
-      float sacc = 0.f;
-      for (int kb = jb; kb < ib; ++kb) {
-        const int k0 = kb * PB;
-        // coalesced loads: consecutive lanes read consecutive rows
-        Ls[tj * (PB + 1) + ti] = (tj < bi) ? A[(i0 + tj) + (int64_t)r * (k0 + ti)] : 0.f;
-        Xs[tj * (PB + 1) + ti] = X[(k0 + tj) + (int64_t)r * (j0 + ti)];
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < PB; ++k) sacc += Ls[ti * (PB + 1) + k] * Xs[k * (PB + 1) + tj];
-        __syncthreads();
+    for (int i = t; i < ROWS; i += kTrsm) {
+      float x[PB];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) x[c] = (c0 + c < r) ? Vs[i * ld + c0 + c] : 0.f;
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        float v = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) v = fmaf(-x[k], Lt[c * (PB + 1) + k], v);
+        x[c] = v / Lt[c * (PB + 1) + c];
       }
-      Ls[ti * (PB + 1) + tj] = sacc;
-      __syncthreads();
-      float v = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < PB; ++k) v -= Di[ti * (PB + 1) + k] * Ls[k * (PB + 1) + tj];
-      Xs[ti * (PB + 1) + tj] = v;
-      __syncthreads();
-      // coalesced store of the block
-      if (tj < bi) X[(i0 + tj) + (int64_t)r * (j0 + ti)] = Xs[tj * (PB + 1) + ti];
-      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < PB; ++c)
+        if (c0 + c < r) Vs[i * ld + c0 + c] = x[c];
     }
-    // diagonal block of X, zero above it
-    if (tj < bi && ti < bi) X[(i0 + tj) + (int64_t)r * (i0 + ti)] = (tj >= ti) ? Di[tj * (PB + 1) + ti] : 0.f;
     __syncthreads();
   }
-  // Rinv(p, q) = Linv(q, p) / d_p for p <= q, 0 below the diagonal
-  for (int64_t e = t; e < (int64_t)r * r; e += kChol) {
-    int q = (int)(e / r), p = (int)(e - (int64_t)q * r);
-    Rinv[e] = (p <= q) ? X[q + (int64_t)r * p] * dinv[p] : 0.f;
+  for (int e = t; e < ROWS * r; e += kTrsm) {
+    int ii = e % ROWS, c = e / ROWS;
+    int64_t row = row0 + ii;
+    if (row < s) {
+      float v = Vs[ii * ld + c];
+      V[row + s * c] = round ? mes::round_tf32(v) : v;
+    }
   }
 }
 
@@ -257,7 +319,7 @@ __global__ void eig_small_kernel(const double* __restrict__ Gin, int n, int r, f
     double off = 0.0;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) off += A[p][q] * A[p][q];
-    if (off <= 1e-30 * scale * scale || scale == 0.0) break;
+    if (off <= 1e-26 * scale * scale || scale == 0.0) break;   // off-norm ~1e-13 relative
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
         if (lane == 0) {
@@ -425,26 +487,55 @@ eig_mid_kernel(const float* __restrict__ Hin, int r, float* __restrict__ Z, cons
 
 namespace mes {
 
-size_t cholinv_smem() { return (1024 + PB * (PB + 1) + 1024 * (PB + 1)) * sizeof(float); }
+size_t chol_smem() { return (1024 + PB * (PB + 1) + 1024 * (PB + 1)) * sizeof(float); }
 
-mes_status cholinv(const float* M, int r, float shift_rel, float* work, float* X, float* Rinv,
-                   int* flags, const int* skip, cudaStream_t st) {
-  if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "cholinv: rank above 1024");
+mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, int* flags, const int* skip,
+                cudaStream_t st) {
+  if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "chol: rank above 1024");
   static bool attr = false;
   if (!attr) {
-    MES_CUDA_TRY(cudaFuncSetAttribute(cholinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)cholinv_smem()));
+    MES_CUDA_TRY(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)chol_smem()));
     attr = true;
   }
   const size_t last = (size_t)r * r * 4 - 1;
-  MES_TRY(audit(M, last, "cholinv M"));
-  MES_TRY(audit(work, last, "cholinv work"));
-  MES_TRY(audit(X, last, "cholinv X"));
-  MES_TRY(audit(Rinv, last, "cholinv Rinv"));
-  ProfScope prof("cholinv_f32", st, 4.0 / 3.0 * r * (double)r * r, 12.0 * r * (double)r);
-  cholinv_kernel<<<1, kChol, cholinv_smem(), st>>>(M, r, shift_rel, work, X, Rinv, flags, skip);
+  MES_TRY(audit(M, last, "chol M"));
+  MES_TRY(audit(L, last, "chol L"));
+  MES_TRY(audit(dinv, (size_t)r * 4 - 1, "chol dinv"));
+  ProfScope prof("chol_f32", st, r * (double)r * r / 3.0, 8.0 * r * (double)r);
+  chol_kernel<<<1, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
+}
+
+template <int ROWS>
+mes_status trsm_launch(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V,
+                       bool round, const int* skip, cudaStream_t st) {
+  const size_t smem = (size_t)(ROWS * (r + 1) + PB * (PB + 1)) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    MES_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      220 * 1024));
+    attr = true;
+  }
+  const unsigned grid = (unsigned)((s + ROWS - 1) / ROWS);
+  trsm_kernel<ROWS><<<grid, kTrsm, smem, st>>>(W, s, r, L, dinv, V, round ? 1 : 0, skip);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V, bool round,
+                const int* skip, cudaStream_t st) {
+  if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "trsm: rank above 1024");
+  if (W == V) return fail(MES_ERR_INVALID_ARG, "trsm: in-place solve not supported");
+  MES_TRY(audit(W, (size_t)(s * r) * 4 - 1, "trsm W"));
+  MES_TRY(audit(V, (size_t)(s * r) * 4 - 1, "trsm V"));
+  MES_TRY(audit(L, (size_t)r * r * 4 - 1, "trsm L"));
+  ProfScope prof("trsm_f32", st, s * (double)r * r, 8.0 * s * r);
+  // rows per CTA: as many as fit in ~200 KB of shared memory
+  if ((size_t)128 * (r + 1) * 4 <= 200 * 1024) return trsm_launch<128>(W, s, r, L, dinv, V, round, skip, st);
+  if ((size_t)64 * (r + 1) * 4 <= 200 * 1024) return trsm_launch<64>(W, s, r, L, dinv, V, round, skip, st);
+  return trsm_launch<32>(W, s, r, L, dinv, V, round, skip, st);
 }
 
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,

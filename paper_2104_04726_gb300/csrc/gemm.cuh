@@ -29,11 +29,16 @@ struct Gemm {
   int64_t c2_m = 0, c2_mh = 0, c2_n = 0, c2_nh = 0, c2_b = 0;
   float alpha = 1.f;
   bool accumulate = false;
+  bool round_tf32 = false;        // store C (and C2) rounded to TF32 (operands of later kind::tf32 products)
   const int* skip = nullptr;      // device flag: when non-zero the launch is a no-op
   // Residual mode: instead of storing, accumulate sum((ref - alpha*AB)^2) in
   // FP64; ref is addressed like C.  partials needs gemm_partials(g) doubles.
   const float* ref = nullptr;
   double* partials = nullptr;
+  // Optional FP32 workspace for split-K (deterministic: partial tiles are
+  // summed in a fixed order).  Used when the tile grid leaves most SMs idle.
+  float* split_ws = nullptr;
+  int64_t split_elems = 0;
 };
 
 // FP32 CUDA-core path.

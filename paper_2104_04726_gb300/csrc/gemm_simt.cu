@@ -43,7 +43,7 @@ __device__ __forceinline__ void store_tile(float (*S)[TILE + 4], const float (&r
 }
 
 template <bool AK, bool BKM, bool RESID>
-__global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
+__global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g, int splits, int64_t tiles_per_split) {
   if (g.skip && *g.skip) return;
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
@@ -51,12 +51,16 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
   const int t = threadIdx.x;
   const int64_t bm = (int64_t)blockIdx.x * BM;
   const int64_t bn = (int64_t)blockIdx.y * BN;
-  const int b = blockIdx.z;
+  const int b = blockIdx.z % g.batch;
+  const int split = blockIdx.z / g.batch;
   const float* A = g.A + (int64_t)b * g.a_b;
   const float* B = g.B + (int64_t)b * g.b_b;
 
   const int64_t nkl = (g.K_lo + BK - 1) / BK;
-  const int64_t tiles = nkl * g.K_hi;
+  const int64_t tt_begin = split * tiles_per_split;
+  int64_t tiles = nkl * g.K_hi - tt_begin;
+  if (tiles > tiles_per_split) tiles = tiles_per_split;
+  int64_t kh_next = tt_begin / nkl, kl_next = (tt_begin - (tt_begin / nkl) * nkl) * BK;
 
   float acc[8][8];
 #pragma unroll
@@ -67,15 +71,14 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
   float ra[8], rb[8];
   int cur = 0;
   if (tiles > 0) {
-    load_tile<AK, BM>(A, g.M, bm, g.a_m, g.a_k, g.a_kh, g.K_lo, 0, 0, ra);
-    load_tile<BKM, BN>(B, g.N, bn, g.b_n, g.b_k, g.b_kh, g.K_lo, 0, 0, rb);
+    load_tile<AK, BM>(A, g.M, bm, g.a_m, g.a_k, g.a_kh, g.K_lo, kh_next, kl_next, ra);
+    load_tile<BKM, BN>(B, g.N, bn, g.b_n, g.b_k, g.b_kh, g.K_lo, kh_next, kl_next, rb);
     store_tile<AK, BM>(As[0], ra);
     store_tile<BKM, BN>(Bs[0], rb);
   }
   __syncthreads();
 
   const int ty = t >> 4, tx = t & 15;
-  int64_t kh_next = 0, kl_next = 0;
   for (int64_t tt = 0; tt < tiles; ++tt) {
     const bool more = tt + 1 < tiles;
     if (more) {
@@ -125,6 +128,20 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
     noff[i] = nl * g.c_n + nh * g.c_nh;
   }
   const int64_t cb = (int64_t)b * g.c_b;
+  if (splits > 1) {
+    float* ws = g.split_ws + ((int64_t)split * g.batch + b) * g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (!mok[i]) continue;
+      int64_t m = bm + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int64_t n = bn + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        if (nok[j]) ws[m * g.N + n] = acc[i][j];
+      }
+    }
+    return;
+  }
   if (RESID) {
     double s = 0.0;
 #pragma unroll
@@ -153,7 +170,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
         if (mok[i] && nok[j]) {
           float* p = g.C + cb + moff[i] + noff[j];
           float v = g.alpha * acc[i][j];
-          *p = g.accumulate ? *p + v : v;
+          v = g.accumulate ? *p + v : v;
+          *p = g.round_tf32 ? mes::round_tf32(v) : v;
         }
     if (g.C2) {
       const int64_t M_lo2 = M_lo, N_lo2 = N_lo;
@@ -167,10 +185,32 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g) {
           if (!nok[j]) continue;
           int64_t n = bn + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
           int64_t nh = n / N_lo2, nl = n - nh * N_lo2;
-          g.C2[(int64_t)b * g.c2_b + ml * g.c2_m + mh * g.c2_mh + nl * g.c2_n + nh * g.c2_nh] = g.alpha * acc[i][j];
+          const float v2 = g.alpha * acc[i][j];
+          g.C2[(int64_t)b * g.c2_b + ml * g.c2_m + mh * g.c2_mh + nl * g.c2_n + nh * g.c2_nh] =
+              g.round_tf32 ? mes::round_tf32(v2) : v2;
         }
       }
     }
+  }
+}
+
+// Fixed-order sum of split-K partial tiles into C (general strides).
+__global__ void split_sum_kernel(const mes::Gemm g, int splits) {
+  if (g.skip && *g.skip) return;
+  const int64_t total = (int64_t)g.batch * g.M * g.N;
+  const int64_t M_lo = g.M_lo > 0 ? g.M_lo : g.M, N_lo = g.N_lo > 0 ? g.N_lo : g.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float sacc = 0.f;
+    for (int sp = 0; sp < splits; ++sp) sacc += g.split_ws[(int64_t)sp * total + e];
+    const int64_t n = e % g.N, bm = e / g.N;
+    const int64_t m = bm % g.M, b = bm / g.M;
+    const int64_t mh = m / M_lo, ml = m - mh * M_lo, nh = n / N_lo, nl = n - nh * N_lo;
+    float v = g.alpha * sacc;
+    float* p = g.C + b * g.c_b + ml * g.c_m + mh * g.c_mh + nl * g.c_n + nh * g.c_nh;
+    v = g.accumulate ? *p + v : v;
+    if (g.round_tf32) v = mes::round_tf32(v);
+    *p = v;
+    if (g.C2) g.C2[b * g.c2_b + ml * g.c2_m + mh * g.c2_mh + nl * g.c2_n + nh * g.c2_nh] = v;
   }
 }
 
@@ -192,13 +232,34 @@ __global__ void sum_doubles_kernel(const double* __restrict__ p, int64_t n, doub
 template <bool AK, bool BKM>
 mes_status launch(const mes::Gemm& g, dim3 grid, cudaStream_t st) {
   const double K = (double)g.K_lo * g.K_hi, bt = g.batch;
-  mes::ProfScope prof("gemm_f32_simt", st, 2.0 * g.M * g.N * K * bt,
-                      4.0 * bt * (g.M * K + g.N * K + g.M * (double)g.N));
-  if (g.ref)
-    gemm_kernel<AK, BKM, true><<<grid, NT, 0, st>>>(g);
-  else
-    gemm_kernel<AK, BKM, false><<<grid, NT, 0, st>>>(g);
-  MES_LAUNCH_CHECK();
+  // split K when the tile grid leaves most SMs idle (not in residual mode)
+  const int64_t nkt = ((g.K_lo + BK - 1) / BK) * g.K_hi;
+  const int64_t tiles = (int64_t)grid.x * grid.y * grid.z;
+  const int64_t sms = mes::sm_count();
+  int splits = 1;
+  if (!g.ref && g.split_ws) {
+    while (tiles * splits * 2 <= sms * 2 && nkt / (splits * 2) >= 8 &&
+           (int64_t)(splits * 2) * g.batch * g.M * g.N <= g.split_elems)
+      splits *= 2;
+  }
+  const int64_t per = (nkt + splits - 1) / splits;
+  splits = (int)((nkt + per - 1) / per);
+  grid.z *= splits;
+  {
+    mes::ProfScope prof("gemm_f32_simt", st, 2.0 * g.M * g.N * K * bt,
+                        4.0 * bt * (g.M * K + g.N * K + g.M * (double)g.N));
+    if (g.ref)
+      gemm_kernel<AK, BKM, true><<<grid, NT, 0, st>>>(g, splits, per);
+    else
+      gemm_kernel<AK, BKM, false><<<grid, NT, 0, st>>>(g, splits, per);
+    MES_LAUNCH_CHECK();
+  }
+  if (splits > 1) {
+    mes::ProfScope prof("split_reduce", st, 0.0, 4.0 * splits * bt * g.M * (double)g.N);
+    const int64_t total = (int64_t)g.batch * g.M * g.N;
+    split_sum_kernel<<<mes::grid_for(total, 256, sms * 8), 256, 0, st>>>(g, splits);
+    MES_LAUNCH_CHECK();
+  }
   return MES_OK;
 }
 

@@ -30,12 +30,14 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 struct TcArgs {
   int64_t M, N;
   int k_tiles_lo, k_tiles_total, kt_per_split, splits, batch;
+  int a_batched, b_batched;   // 0: operand shared by all batches (coordinate 0)
   float* C;
   int64_t M_lo, c_m, c_mh, N_lo, c_n, c_nh, c_b;
   float* C2;
   int64_t c2_m, c2_mh, c2_n, c2_nh, c2_b;
   float alpha;
   int accumulate;
+  int round_out;
   const float* ref;
   double* partials;
   float* split_ws;     // [split][batch][M][N] when splits > 1
@@ -215,8 +217,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 0 ? 4 : 2));
       uint8_t* sa = tiles + stage * C::STAGE;
       mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
-      tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, b);
-      tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, b);
+      tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
+      tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
       if (++stage == STAGES) {
         stage = 0;
         phase ^= 1u;
@@ -283,8 +285,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
           sq += (double)d * (double)d;
         } else {
           float* p = args.C + moff + nl * args.c_n + nh * args.c_nh;
-          *p = args.accumulate ? *p + val : val;
-          if (args.C2) args.C2[moff2 + nl * args.c2_n + nh * args.c2_nh] = val;
+          float v = args.accumulate ? *p + val : val;
+          if (args.round_out) v = mes::round_tf32(v);
+          *p = v;
+          if (args.C2) args.C2[moff2 + nl * args.c2_n + nh * args.c2_nh] = args.round_out ? mes::round_tf32(val) : val;
         }
       }
     }
@@ -317,9 +321,11 @@ __global__ void split_reduce_kernel(const float* __restrict__ ws, TcArgs a) {
     const int64_t bm = e / a.N;
     const int64_t m = bm % a.M, b = bm / a.M;
     const int64_t mh = m / a.M_lo, ml = m - mh * a.M_lo, nh = n / a.N_lo, nl = n - nh * a.N_lo;
-    const float val = a.alpha * s;
+    float val = a.alpha * s;
     float* p = a.C + ml * a.c_m + mh * a.c_mh + nl * a.c_n + nh * a.c_nh + b * a.c_b;
-    *p = a.accumulate ? *p + val : val;
+    val = a.accumulate ? *p + val : val;
+    if (a.round_out) val = mes::round_tf32(val);
+    *p = val;
     if (a.C2) a.C2[ml * a.c2_m + mh * a.c2_mh + nl * a.c2_n + nh * a.c2_nh + b * a.c2_b] = val;
   }
 }
@@ -391,6 +397,7 @@ bool tc_eligible(const Gemm& g, int kind) {
   if ((g.a_m * E) % 16 || (g.b_n * E) % 16) return false;
   if (g.K_hi > 1 && ((g.a_kh * E) % 16 || (g.b_kh * E) % 16)) return false;
   if (g.batch > 1 && (((g.a_b * E) % 16) || ((g.b_b * E) % 16))) return false;
+  if (g.a_b < 0 || g.b_b < 0 || g.a_kh < 0 || g.b_kh < 0) return false;
   if (reinterpret_cast<uintptr_t>(g.A) % 16 || reinterpret_cast<uintptr_t>(g.B) % 16) return false;
   if (g.M > INT32_MAX || g.N > INT32_MAX || g.K_lo > INT32_MAX) return false;
   return true;
@@ -403,8 +410,9 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   const int BK = 128 / (kind == 0 ? 4 : 2);
   const int bn = g.N > 128 ? 256 : 128;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, g.batch, g.a_m, g.a_kh, g.a_b, BM) ||
-      !make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, g.batch, g.b_n, g.b_kh, g.b_b, bn))
+  const bool ab = g.batch > 1 && g.a_b != 0, bb = g.batch > 1 && g.b_b != 0;
+  if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
+      !make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh, g.b_b, bn))
     return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map rejected");
   TcArgs a;
   a.M = g.M;
@@ -412,6 +420,8 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   a.k_tiles_lo = (int)((g.K_lo + BK - 1) / BK);
   a.k_tiles_total = a.k_tiles_lo * (int)g.K_hi;
   a.batch = g.batch;
+  a.a_batched = ab ? 1 : 0;
+  a.b_batched = bb ? 1 : 0;
   a.C = g.C;
   a.M_lo = g.M_lo > 0 ? g.M_lo : g.M;
   a.c_m = g.c_m; a.c_mh = g.c_mh;
@@ -421,6 +431,7 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   a.c2_m = g.c2_m; a.c2_mh = g.c2_mh; a.c2_n = g.c2_n; a.c2_nh = g.c2_nh; a.c2_b = g.c2_b;
   a.alpha = g.alpha;
   a.accumulate = g.accumulate ? 1 : 0;
+  a.round_out = g.round_tf32 ? 1 : 0;
   a.ref = g.ref;
   a.partials = g.partials;
   a.skip = g.skip;

@@ -31,7 +31,8 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 // XB[y + s2*(x + s1*l)] = X[x + s1*(y + s2*l)], 32x32 tiles; norm partials.
 __global__ void __launch_bounds__(kT)
 slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int64_t L,
-                       float* __restrict__ XB, double* __restrict__ partials) {
+                       float* __restrict__ XB, double* __restrict__ partials, float* __restrict__ Xr,
+                       int round) {
   __shared__ float tile[32][33];
   __shared__ double red[kT / 32];
   const int64_t tx = (s1 + 31) / 32, ty = (s2 + 31) / 32;
@@ -47,8 +48,10 @@ slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int6
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
       int64_t x = bx * 32 + c, y = by * 32 + rr;
       float v = (x < s1 && y < s2) ? src[x + s1 * y] : 0.f;
-      tile[rr][c] = v;
       acc += (double)v * v;
+      if (round) v = mes::round_tf32(v);
+      if (Xr && x < s1 && y < s2) Xr[l * s1 * s2 + x + s1 * y] = v;
+      tile[rr][c] = v;
     }
     __syncthreads();
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
@@ -273,14 +276,28 @@ __global__ void permute_core_kernel(const float* __restrict__ in, int64_t total,
   }
 }
 
+__global__ void round_copy_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t n,
+                                  const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mes::round_tf32(in[i]);
+}
+
 }  // namespace
 
 namespace mes {
 
 mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
-                           double* partials, int nblocks, cudaStream_t st) {
-  ProfScope prof("slice_transpose", st, 0.0, 8.0 * s1 * s2 * L);
-  slice_transpose_kernel<<<nblocks, kT, 0, st>>>(X, s1, s2, L, XB, partials);
+                           double* partials, int nblocks, cudaStream_t st, float* Xr, bool round) {
+  ProfScope prof("slice_transpose", st, 0.0, (Xr ? 12.0 : 8.0) * s1 * s2 * L);
+  slice_transpose_kernel<<<nblocks, kT, 0, st>>>(X, s1, s2, L, XB, partials, Xr, round ? 1 : 0);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status round_copy(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st) {
+  ProfScope prof("round_copy", st, 0.0, 8.0 * n);
+  round_copy_kernel<<<grid_for(n, kT, 1024), kT, 0, st>>>(in, out, n, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

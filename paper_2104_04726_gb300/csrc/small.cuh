@@ -30,8 +30,13 @@ struct KronDesc {
 };
 mes_status kron_build(const KronDesc& d, float* K, const int* skip, cudaStream_t st);
 
+// XB = per-slice transpose of X (and ||X||^2 partials); with `round`, XB and
+// the optional copy Xr hold X rounded to TF32.
 mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
-                           double* partials, int nblocks, cudaStream_t st);
+                           double* partials, int nblocks, cudaStream_t st, float* Xr = nullptr,
+                           bool round = false);
+// out = round_tf32(in), elementwise
+mes_status round_copy(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st);
 mes_status sumsq(const float* x, int64_t n, double* partials, int nblocks, const int* skip,
                  cudaStream_t st);
 mes_status uniform_fill(float* out, int64_t n, uint64_t seed, cudaStream_t st);
@@ -51,8 +56,12 @@ mes_status permute_core(const float* in, int64_t total, int64_t stride, int r, c
                         const float* sign, float* out, cudaStream_t st);
 
 // dense.cu
-mes_status cholinv(const float* M, int r, float shift_rel, float* work, float* X, float* Rinv,
-                   int* flags, const int* skip, cudaStream_t st);
+// Shifted Cholesky of an r x r Gram (L, dinv, inverted diagonal blocks) and
+// the right-side solve V = W D^-1 L^-T that completes one CholeskyQR pass.
+mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, int* flags, const int* skip,
+                cudaStream_t st);
+mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V, bool round,
+                const int* skip, cudaStream_t st);
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,
                      cudaStream_t st);
 mes_status eig_mid(const float* H, int r, float* Z, const int* skip, cudaStream_t st);

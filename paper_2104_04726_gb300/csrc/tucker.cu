@@ -38,6 +38,7 @@
 #include <cstring>
 
 #include "gemm.cuh"
+#include "gemm_tc.cuh"
 #include "small.cuh"
 
 namespace {
@@ -108,20 +109,41 @@ struct Driver {
   cudaStream_t st;
   mes::Scratch* scr;
   const int* skip = nullptr;       // device stop flag, null outside the sweeps
-  int* flags = nullptr;            // numerics flags (cholinv pivots)
+  int* flags = nullptr;            // numerics flags (Cholesky pivots, pipeline waits)
 
   float *cwA = nullptr, *cwX = nullptr, *H = nullptr, *Rinv = nullptr;
+  float* dinv = nullptr;                    // equilibration of chol
   float *W = nullptr, *W2 = nullptr, *Z = nullptr, *Zh = nullptr, *Kmat = nullptr;
   double *gpart = nullptr, *G64 = nullptr;
 
+  int prec = MES_PREC_FP32;
+  float* split_ws = nullptr;
+  int64_t split_elems = 0;
+
+  // precision-critical products (Grams of the factor update): FP32 CUDA cores
   mes_status gemm(const Gemm& g) {
     Gemm h = g;
     h.skip = skip;
+    h.split_ws = split_ws;
+    h.split_elems = split_elems;
     return mes::gemm_f32(h, st);
   }
 
-  // S (s x r) := orth(W) by three passes of CholeskyQR, the first shifted.
-  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout) {
+  // the large contractions: tensor cores in the TF32 form when the operands
+  // are K-major and TMA-addressable, CUDA cores otherwise
+  mes_status big(const Gemm& g) {
+    Gemm h = g;
+    h.skip = skip;
+    if (prec == MES_PREC_TF32 && mes::tc_eligible(h, 0))
+      return mes::gemm_tc(h, 0, split_ws, split_elems, flags, st);
+    h.split_ws = split_ws;
+    h.split_elems = split_elems;
+    return mes::gemm_f32(h, st);
+  }
+
+  // S (s x r) := orth(W) by three passes of CholeskyQR, the first shifted;
+  // in the TF32 form Srnd receives S rounded to TF32 (the tensor-core operand).
+  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout, float* Srnd) {
     float* src = Win;
     float* bufs[2] = {W2, Win};
     for (int pass = 0; pass < 3; ++pass) {
@@ -132,27 +154,23 @@ struct Driver {
       g.B = src; g.b_n = s; g.b_k = 1;
       g.C = H; g.c_m = 1; g.c_n = r;
       MES_TRY(gemm(g));
-      MES_TRY(mes::cholinv(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, cwX, Rinv, flags, skip, st));
-      Gemm a = base();  // dst = src * Rinv
-      a.M = s; a.N = r; a.K_lo = r;
-      a.A = src; a.a_m = 1; a.a_k = s;
-      a.B = Rinv; a.b_n = r; a.b_k = 1;
-      a.C = dst; a.c_m = 1; a.c_n = s;
-      MES_TRY(gemm(a));
+      MES_TRY(mes::chol(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, dinv, flags, skip, st));
+      MES_TRY(mes::trsm(src, s, (int)r, cwA, dinv, dst, false, skip, st));   // dst = src R^-1
       src = dst;
     }
+    if (prec == MES_PREC_TF32 && Srnd) MES_TRY(mes::round_copy(Sout, Srnd, s * r, skip, st));
     return MES_OK;
   }
 
   // One subspace step for a large mode: Y is given through two GEMM operand
   // descriptions (Yt: Z = Y^T S,  Yn: W = Y Zh), J = number of columns of Y_(n).
   mes_status subspace_step(const Gemm& zdesc, const Gemm& wdesc, int64_t J, int64_t s, int64_t r,
-                           float* S) {
+                           float* S, float* Srnd) {
     // Z = Y^T S   (J x r, stored Z[j + J*q])
     Gemm gz = zdesc;
-    gz.B = S; gz.b_n = s; gz.b_k = 1;
+    gz.B = (prec == MES_PREC_TF32) ? Srnd : S; gz.b_n = s; gz.b_k = 1;
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
-    MES_TRY(gemm(gz));
+    MES_TRY(big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
     Gemm gh = base();
     gh.M = r; gh.N = r; gh.K_lo = J;
@@ -160,18 +178,14 @@ struct Driver {
     gh.B = Z; gh.b_n = J; gh.b_k = 1;
     gh.C = H; gh.c_m = 1; gh.c_n = r;
     MES_TRY(gemm(gh));
-    MES_TRY(mes::cholinv(H, (int)r, kShiftZ, cwA, cwX, Rinv, flags, skip, st));
-    Gemm ga = base();
-    ga.M = J; ga.N = r; ga.K_lo = r;
-    ga.A = Z; ga.a_m = 1; ga.a_k = J;
-    ga.B = Rinv; ga.b_n = r; ga.b_k = 1;
-    ga.C = Zh; ga.c_m = 1; ga.c_n = J;
-    MES_TRY(gemm(ga));
+    MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, flags, skip, st));
+    // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in that form
+    MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, Zh, prec == MES_PREC_TF32, skip, st));
     // W = Y Zh   (s x r)
     Gemm gw = wdesc;
     gw.C = W; gw.c_m = 1; gw.c_n = s;
-    MES_TRY(gemm(gw));
-    return orth(W, s, r, S);
+    MES_TRY(big(gw));
+    return orth(W, s, r, S, Srnd);
   }
 
   // Small-mode Gram (FP64) of fibres projected by the Kronecker matrix built
@@ -191,8 +205,54 @@ struct Driver {
 // residual against `ref`.
 mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float* const* fac, float* out,
                                 const float* ref, double* sse, mes::Scratch& scr, float* T1, float* T2,
-                                float* Kmat, cudaStream_t st) {
+                                float* Kmat, cudaStream_t st, int prec = MES_PREC_FP32, int* err = nullptr) {
   const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
+  if (prec == MES_PREC_TF32) {
+    // tensor-core form: the same two products with K-major operands, reading
+    // transposed copies of S1 and S2 (S^T stored with the rank index fastest)
+    float *U0t, *U1t;
+    MES_TRY(scr.alloc(&U0t, s1 * r1));
+    MES_TRY(scr.alloc(&U1t, s2 * r2));
+    MES_TRY(mes::slice_transpose(fac[0], s1, r1, 1, U0t, nullptr, 64, st));
+    MES_TRY(mes::slice_transpose(fac[1], s2, r2, 1, U1t, nullptr, 64, st));
+    KronDesc kd;
+    kd.nm = sh.nsm;
+    for (int m = 0; m < sh.nsm; ++m) {
+      kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'N'; kd.U[m] = fac[m + 2];
+    }
+    MES_TRY(mes::kron_build(kd, Kmat, nullptr, st));
+    Fibres fb;
+    fb.F_lo = r1; fb.F_hi = r2;
+    fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
+    fb.out = T1; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
+    MES_TRY(mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st));
+    Gemm g = Gemm();   // T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2t[q2 + r2 y]
+    g.M = r1; g.N = s2; g.K_lo = r2; g.batch = (int)L;
+    g.A = T1; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
+    g.B = U1t; g.b_n = r2; g.b_k = 1; g.b_b = 0;
+    g.C = T2; g.c_m = 1; g.c_n = r1; g.c_b = r1 * s2;
+    Gemm h = Gemm();   // out[x + s1 n] = sum_q1 S1t[q1 + r1 x] T2[q1 + r1 n]
+    h.M = s1; h.N = s2 * L; h.K_lo = r1;
+    h.A = U0t; h.a_m = r1; h.a_k = 1;
+    h.B = T2; h.b_n = r1; h.b_k = 1;
+    h.C = out; h.c_m = 1; h.c_n = s1;
+    if (mes::tc_eligible(g, 0) && mes::tc_eligible(h, 0)) {
+      MES_TRY(mes::gemm_tc(g, 0, nullptr, 0, err, st));
+      if (out) MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
+      if (ref && sse) {
+        double* part = nullptr;
+        const int64_t np = mes::gemm_partials(h) * 2 + 16;   // TC tiles are 128 x 128 or 128 x 256
+        MES_TRY(scr.alloc(&part, np));
+        MES_CUDA_TRY(cudaMemsetAsync(part, 0, np * sizeof(double), st));
+        h.ref = ref;
+        h.C = nullptr;
+        h.partials = part;
+        MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
+        MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
+      }
+      return MES_OK;
+    }
+  }
   // T1[q2 + r2 q1 + r1 r2 l] = (Q x_{n>=3} S_n)
   KronDesc kd;
   kd.nm = sh.nsm;
@@ -260,10 +320,10 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   const int precision = o.precision;
-  if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_BF16X3)
+  if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_TF32)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: unknown precision %d", precision);
-  if (precision != MES_PREC_FP32)
-    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "mes_tucker_als: tensor-core precision forms not built");
+  if (precision == MES_PREC_BF16)
+    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "mes_tucker_als: the BF16 form is not built yet");
   const int init_iters = o.init_iters > 0 ? o.init_iters : 4;
   const int inner_iters = o.inner_iters > 0 ? o.inner_iters : 2;
   const uint64_t seed = o.seed ? o.seed : 1;
@@ -303,8 +363,24 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   int* order;
   const int nblk = (int)mes::grid_for(nel, 256, (int64_t)mes::sm_count() * 4);
   MES_TRY(scr.alloc(&XB, nel));
+  float *Pt, *Cat, *Xr = nullptr, *Ur[2] = {nullptr, nullptr};
+  const bool tf32 = precision == MES_PREC_TF32;
+  if (tf32) {
+    // operands of the kind::tf32 products, pre-rounded to nearest TF32
+    MES_TRY(scr.alloc(&Xr, nel));
+    MES_TRY(scr.alloc(&Ur[0], s1 * r1));
+    MES_TRY(scr.alloc(&Ur[1], s2 * r2));
+  }
   MES_TRY(scr.alloc(&P, s1 * r2 * L));
   MES_TRY(scr.alloc(&Ca, s2 * r1 * L));
+  MES_TRY(scr.alloc(&Pt, s1 * r2 * L));
+  MES_TRY(scr.alloc(&Cat, s2 * r1 * L));
+  d.prec = precision;
+  {
+    int64_t ws = s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2;
+    d.split_elems = 16 * ws;
+    MES_TRY(scr.alloc(&d.split_ws, d.split_elems));
+  }
   MES_TRY(scr.alloc(&Bt, r1 * L * r2));
   if (!sh.small_full) {
     MES_TRY(scr.alloc(&Y0, s1 * J0));
@@ -321,6 +397,7 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   MES_TRY(scr.alloc(&d.Rinv, rmax * rmax));
   MES_TRY(scr.alloc(&d.cwA, rmax * rmax));
   MES_TRY(scr.alloc(&d.cwX, rmax * rmax));
+  MES_TRY(scr.alloc(&d.dinv, rmax));
   MES_TRY(scr.alloc(&d.Kmat, 16384));
   MES_TRY(scr.alloc(&d.gpart, (size_t)mes::small_gram_blocks(s1 * s2) * 1024));
   MES_TRY(scr.alloc(&d.G64, 1024));
@@ -342,7 +419,8 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   float* U1 = factors[1];
 
   // ---- second layout of T and ||T||^2 ----
-  MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st));
+  MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st, Xr, tf32));
+  const float* Xop = tf32 ? Xr : X;    // T as an operand of the large products
   MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
 
   // ---- initialisation: truncated HOSVD (Eq. 6, Eq. 7) or given factors ----
@@ -351,6 +429,7 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       if (!o.init_factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: init_factors[%d] null", n);
       MES_CUDA_TRY(cudaMemcpyAsync(factors[n], o.init_factors[n], sizeof(float) * sh.s[n] * sh.r[n],
                                    cudaMemcpyDeviceToDevice, st));
+      if (tf32 && n < 2) MES_TRY(mes::round_copy(factors[n], Ur[n], sh.s[n] * sh.r[n], nullptr, st));
     }
   } else {
     // small modes: exact eigenvectors of the unfolding Grams of T
@@ -373,13 +452,13 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
       float* S = factors[n];
       MES_TRY(mes::uniform_fill(d.W, s * r, seed * 2 + n, st));
-      MES_TRY(d.orth(d.W, s, r, S));
+      MES_TRY(d.orth(d.W, s, r, S, Ur[n]));
       Gemm gz = base(), gw = base();
       int64_t J;
       if (n == 0) {
         J = s2 * L;   // Z[(y,l)][q] = sum_x T[x + s1*(y,l)] S[x,q]
         gz.M = J; gz.N = r; gz.K_lo = s1;
-        gz.A = X; gz.a_m = s1; gz.a_k = 1;
+        gz.A = Xop; gz.a_m = s1; gz.a_k = 1;
         // W[x][q] = sum_{y,l} XB[y + s2*x + s1*s2*l] Zh[(y + s2*l) + J*q]
         gw.M = s1; gw.N = r; gw.K_lo = s2; gw.K_hi = L;
         gw.A = XB; gw.a_m = s2; gw.a_k = 1; gw.a_kh = s1 * s2;
@@ -390,10 +469,10 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
         gz.A = XB; gz.a_m = s2; gz.a_k = 1;
         // W[y][q] = sum_{x,l} X[x + s1*y + s1*s2*l] Zh[(x + s1*l) + J*q]
         gw.M = s2; gw.N = r; gw.K_lo = s1; gw.K_hi = L;
-        gw.A = X; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
+        gw.A = Xop; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
         gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s1;
       }
-      for (int it = 0; it < init_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s, r, S));
+      for (int it = 0; it < init_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s, r, S, Ur[n]));
     }
   }
 
@@ -405,9 +484,12 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       Gemm g = base();
       g.M = s1; g.N = r2; g.K_lo = s2; g.batch = (int)L;
       g.A = XB; g.a_m = s2; g.a_k = 1; g.a_b = s1 * s2;
-      g.B = U1; g.b_n = s2; g.b_k = 1; g.b_b = 0;
+      g.B = tf32 ? Ur[1] : U1; g.b_n = s2; g.b_k = 1; g.b_b = 0;
       g.C = P; g.c_m = r2 * L; g.c_n = 1; g.c_b = r2;
-      MES_TRY(d.gemm(g));
+      g.round_tf32 = tf32;
+      // second layout Pt[x + s1 (q2 + r2 l)]: the K-major operand of Z below
+      g.C2 = Pt; g.c2_m = 1; g.c2_n = s1; g.c2_b = s1 * r2;
+      MES_TRY(d.big(g));
       const float* Y = P;
       if (!sh.small_full) {
         KronDesc kd;
@@ -426,20 +508,27 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       const int64_t J = sh.small_full ? r2 * L : J0;
       Gemm gz = base(), gw = base();
       gz.M = J; gz.N = r1; gz.K_lo = s1;          // Z[j][q] = sum_x Y[j + J x] S[x][q]
-      gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      if (sh.small_full) {
+        gz.A = Pt; gz.a_m = s1; gz.a_k = 1;
+      } else {
+        gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      }
       gw.M = s1; gw.N = r1; gw.K_lo = J;          // W[x][q] = sum_j Y[j + J x] Zh[j + J q]
       gw.A = Y; gw.a_m = J; gw.a_k = 1;
       gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
-      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s1, r1, U0));
+      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s1, r1, U0, Ur[0]));
     }
     // mode 2: Ca = T x_1 S1^T: Ca[(q1 + r1 l) + r1 L y] = sum_x U0[x + s1 q1] X[x + s1 (y + s2 l)]
     {
       Gemm g = base();
       g.M = r1; g.N = s2 * L; g.K_lo = s1;
-      g.A = U0; g.a_m = s1; g.a_k = 1;
-      g.B = X; g.b_n = s1; g.b_k = 1;
+      g.A = tf32 ? Ur[0] : U0; g.a_m = s1; g.a_k = 1;
+      g.B = Xop; g.b_n = s1; g.b_k = 1;
       g.C = Ca; g.c_m = 1; g.N_lo = s2; g.c_n = r1 * L; g.c_nh = r1;
-      MES_TRY(d.gemm(g));
+      g.round_tf32 = tf32;
+      // second layout Cat[y + s2 (q1 + r1 l)]: K-major operand of Z and B
+      g.C2 = Cat; g.c2_m = s2; g.c2_n = 1; g.c2_nh = s2 * r1;
+      MES_TRY(d.big(g));
       const float* Y = Ca;
       if (!sh.small_full) {
         KronDesc kd;
@@ -457,21 +546,25 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       }
       const int64_t J = sh.small_full ? r1 * L : J1;
       Gemm gz = base(), gw = base();
-      gz.M = J; gz.N = r2; gz.K_lo = s2;
-      gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      gz.M = J; gz.N = r2; gz.K_lo = s2;         // Z[j][q] = sum_y Y[j + J y] S[y][q]
+      if (sh.small_full) {
+        gz.A = Cat; gz.a_m = s2; gz.a_k = 1;
+      } else {
+        gz.A = Y; gz.a_m = 1; gz.a_k = J;
+      }
       gw.M = s2; gw.N = r2; gw.K_lo = J;
       gw.A = Y; gw.a_m = J; gw.a_k = 1;
       gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
-      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1));
+      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1, Ur[1]));
     }
-    // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Ca[(q1 + r1 l) + r1 L y] U1[y + s2 q2]
+    // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Cat[y + s2 (q1 + r1 l)] U1[y + s2 q2]
     {
       Gemm g = base();
       g.M = r1 * L; g.N = r2; g.K_lo = s2;
-      g.A = Ca; g.a_m = 1; g.a_k = r1 * L;
-      g.B = U1; g.b_n = s2; g.b_k = 1;
+      g.A = Cat; g.a_m = s2; g.a_k = 1;
+      g.B = tf32 ? Ur[1] : U1; g.b_n = s2; g.b_k = 1;
       g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
-      MES_TRY(d.gemm(g));
+      MES_TRY(d.big(g));
     }
     // small modes n = 3..N: Gram of B x_{m != n} S_m^T, exact eigenvectors
     for (int n = 2; n < N; ++n) {
@@ -537,13 +630,8 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
         gzz.B = d.cwX; gzz.b_n = r; gzz.b_k = 1;
         gzz.C = d.H; gzz.c_m = 1; gzz.c_n = r;
         MES_TRY(d.gemm(gzz));
-        MES_TRY(mes::cholinv(d.H, (int)r, 0.f, d.cwA, d.Rinv, d.W2, flags, nullptr, st));
-        Gemm gzr = base();
-        gzr.M = r; gzr.N = r; gzr.K_lo = r;
-        gzr.A = d.cwX; gzr.a_m = 1; gzr.a_k = r;
-        gzr.B = d.W2; gzr.b_n = r; gzr.b_k = 1;
-        gzr.C = d.Rinv; gzr.c_m = 1; gzr.c_n = r;
-        MES_TRY(d.gemm(gzr));                                       // Z in Rinv
+        MES_TRY(mes::chol(d.H, (int)r, 0.f, d.cwA, d.dinv, flags, nullptr, st));
+        MES_TRY(mes::trsm(d.cwX, r, (int)r, d.cwA, d.dinv, d.Rinv, false, nullptr, st));   // Z in Rinv
         Gemm gu = base();  // W = S Z
         gu.M = s; gu.N = r; gu.K_lo = r;
         gu.A = S; gu.a_m = 1; gu.a_k = s;
@@ -590,7 +678,9 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   if (fit) {
     const float* fac[8];
     for (int n = 0; n < N; ++n) fac[n] = factors[n];
-    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st));
+    // evaluated in FP32 in every form: a TF32 reconstruction would add its own
+    // rounding (~1e-3 relative per entry) to the residual being measured
+    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st, MES_PREC_FP32, flags));
     MES_TRY(mes::final_fit(normX, sse, fit, st));
   }
   return MES_OK;

@@ -4,11 +4,11 @@ CUDA-core FP32, tcgen05 kind::tf32 and kind::f16 (BF16), against numpy.
 Tolerances follow the arithmetic of each kind, for N(0,1) inputs (partial
 sums grow like sqrt(k)): sequential FP32 accumulation of K products has an
 error of about 2^-24 * K / sqrt(2) per output, so the max over all outputs
-stays below 4 * 2^-24 * K; kind::tf32 keeps 10 explicit mantissa bits of each
+stays below 6 * 2^-24 * K; kind::tf32 keeps 10 explicit mantissa bits of each
 input (relative error up to 2^-10 per operand, about 2e-3 per product), a
 random sum of K of them stays below 8e-3 * sqrt(K); kind::f16 on
 BF16-rounded inputs is compared with the product of the same rounded inputs,
-so only the FP32 accumulation differs (4 * 2^-24 * K)."""
+so only the FP32 accumulation differs (6 * 2^-24 * K)."""
 import ctypes
 
 import numpy as np
@@ -59,13 +59,13 @@ def test_gemm_kernels(lib, impl, M, N, K, batch):
     u = 2.0 ** -24
     if impl == 2:
         Ar, Br = _bf16(A), _bf16(B)
-        tol = 4 * u * K + 1e-6
+        tol = 6 * u * K + 1e-6
     elif impl == 1:
         Ar, Br = A, B
         tol = 8e-3 * np.sqrt(K)
     else:
         Ar, Br = A, B
-        tol = 4 * u * K + 1e-6
+        tol = 6 * u * K + 1e-6
     if impl == 2 and (K * 2) % 16:
         # BF16 rows of K elements are not a multiple of 16 bytes: the tensor
         # map cannot address them and the call must say so
