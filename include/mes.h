@@ -177,6 +177,36 @@ mes_status mes_reconstruct(const float* core, const float* const* factors, int N
 mes_status mes_quantize_core(const float* core, int N, const int64_t* ranks, int bits,
                              int16_t* q, float* scales, int status_host_sync, void* stream);
 
+/*
+ * mes_quantize_core_noalloc -- the quantiser of mes_quantize_core for callers
+ * that cannot allocate device memory.  The paper has no counterpart; this is
+ * an engineering variant.  Same arguments, layouts, arithmetic and results as
+ * mes_quantize_core (bit-identical codes and scales), without the NaN/Inf
+ * report (a non-finite plane gets scale NaN).
+ *
+ * Who needs it: code that must not call the device allocator once it is
+ * running -- a serving or streaming loop with a fixed memory budget, or a host
+ * program that gives the library only buffers it owns -- cannot use
+ * mes_quantize_core, whose per-plane scratch comes from cudaMallocAsync.
+ * Here that scratch is a fixed array of 4096 words (16 KiB) in device global
+ * memory, part of the library image: every GPU that loads the library holds
+ * it until the process exits.  The call allocates nothing and calls no
+ * allocating routine.
+ *
+ * Limits and behaviour:
+ *  - at most 4096 planes (prod_{n>=3} r_n); more gives MES_ERR_INVALID_ARG;
+ *  - the first call on a device looks up the array's device address (once
+ *    per device, with that device current) -- make that first call before
+ *    any stream capture;
+ *  - every call shares the one array: calls whose work overlaps on the GPU
+ *    (different streams without ordering) race and give wrong results; calls
+ *    ordered on one stream are safe;
+ *  - the array keeps the previous call's contents; each call clears the
+ *    words it uses before using them.
+ */
+mes_status mes_quantize_core_noalloc(const float* core, int N, const int64_t* ranks, int bits,
+                                     int16_t* q, float* scales, void* stream);
+
 /* Inverse of mes_quantize_core: x = q * scale (FP32), same layouts. */
 mes_status mes_dequantize_core(const int16_t* q, const float* scales, int N,
                                const int64_t* ranks, float* core, void* stream);

@@ -36,6 +36,7 @@ SIGNATURES = {
     "mes_reconstruct": (_c.c_int, [_p, _c.POINTER(_p), _c.c_int, _i64p, _i64p, _p, _p, _p, _p]),
     "mes_quantize_core": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _c.c_int, _p]),
     "mes_dequantize_core": (_c.c_int, [_p, _p, _c.c_int, _i64p, _p, _p]),
+    "mes_quantize_core_noalloc": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _p]),
     "mes_gemm_selftest": (_c.c_int, [_c.c_int, _p, _p, _p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _p]),
     "mes_profile_enable": (None, [_c.c_int]),
     "mes_profile_count": (_c.c_int, []),
