@@ -94,8 +94,8 @@ typedef struct mes_als_opts {
   int precision;        /* mes_precision of the large contractions (FP32).
                            The Gram and orthonormalisation products of the
                            factor update stay FP32 in every form.           */
-  int init_iters;       /* subspace steps of the T-HOSVD initialisation (4)   */
-  int inner_iters;      /* subspace steps per factor update in a sweep (2)    */
+  int init_iters;       /* subspace steps of the T-HOSVD initialisation (2)   */
+  int inner_iters;      /* subspace steps per factor update in a sweep (1)    */
   uint64_t seed;        /* seed of the random start block of the init (1)     */
   const float* const* init_factors; /* nullable: device factors to start from
                                        instead of T-HOSVD (warm start / resume) */

@@ -13,7 +13,13 @@
 // GB300's FP64 rate is a small fraction of its FP32 rate, so O(r^3) work at
 // r in the hundreds runs in FP32; FP64 is used where the work is O(n^3) with
 // n <= 32 and for accumulations.
+#include <cooperative_groups.h>
+#include <cstdio>
+#include <cstdlib>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -21,7 +27,7 @@ constexpr int PB = 32;
 
 // --------------------------------------------------------------------------
 // chol: equilibrated, shifted Cholesky of a symmetric r x r Gram M (one CTA,
-// 512 threads).  A = D^-1 M D^-1 + shift * r * I = L L^T with D = diag(M)^1/2.
+// 256 threads).  A = D^-1 M D^-1 + shift * r * I = L L^T with D = diag(M)^1/2.
 // Outputs L (lower triangle of `L`, column-major) and dinv = 1 / diag(D).
 // Blocked by 32 columns: the diagonal block is factored by one warp in
 // registers, the panel below is solved by forward substitution (one row per
@@ -30,17 +36,15 @@ constexpr int PB = 32;
 // pivot falls below max(1e-7, 0.1 * shift): it must dominate the FP32
 // rounding of the Gram, yet stay small so the next pass is well conditioned.
 // --------------------------------------------------------------------------
-constexpr int kChol = 512;
+constexpr int kChol = 256;
 
-__device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad) {
-  const int lane = threadIdx.x & 31;
-  float row[PB];
-#pragma unroll
-  for (int k = 0; k < PB; ++k) row[k] = (k <= lane && lane < b && k < b) ? Dg[lane * (PB + 1) + k] : (k == lane ? 1.f : 0.f);
-#pragma unroll
-  for (int j = 0; j < PB; ++j) {
-    float piv = __shfl_sync(0xffffffffu, row[j], j);
-    if (j < b) {
+// One column step of the 32 x 32 factorization held one row per lane in
+// registers; J is a compile-time index so row[] never spills to local memory.
+template <int J>
+__device__ __forceinline__ void chol_step(float (&row)[PB], int lane, int b, float floor, int* bad) {
+  if constexpr (J < PB) {
+    float piv = __shfl_sync(0xffffffffu, row[J], J);
+    if (J < b) {
       if (!(piv > floor)) {
         if (lane == 0) *bad = 1;
         piv = floor;
@@ -48,16 +52,25 @@ __device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* 
     } else {
       piv = 1.f;
     }
-    piv = sqrtf(piv);
-    if (lane == j) row[j] = piv;
-    else if (lane > j) row[j] /= piv;
-    const float lij = row[j];
+    const float rs = rsqrtf(piv);
+    if (lane == J) row[J] = piv * rs;
+    else if (lane > J) row[J] *= rs;
+    const float lij = row[J];
 #pragma unroll
-    for (int k = j + 1; k < PB; ++k) {
-      const float lkj = __shfl_sync(0xffffffffu, row[j], k);
-      if (lane >= k) row[k] -= lij * lkj;
+    for (int k = J + 1; k < PB; ++k) {
+      const float lkj = __shfl_sync(0xffffffffu, row[J], k);
+      if (lane >= k) row[k] = fmaf(-lij, lkj, row[k]);
     }
+    chol_step<J + 1>(row, lane, b, floor, bad);
   }
+}
+
+__device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad) {
+  const int lane = threadIdx.x & 31;
+  float row[PB];
+#pragma unroll
+  for (int k = 0; k < PB; ++k) row[k] = (k <= lane && lane < b && k < b) ? Dg[lane * (PB + 1) + k] : (k == lane ? 1.f : 0.f);
+  chol_step<0>(row, lane, b, floor, bad);
 #pragma unroll
   for (int k = 0; k < PB; ++k) Dg[lane * (PB + 1) + k] = (k <= lane) ? row[k] : 0.f;
 }
@@ -72,6 +85,8 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
   float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
   __shared__ int bad;
   const int t = threadIdx.x, warp = t >> 5;
+  // flags[0]: error bits; flags[1]: calls; flags[2]: shift restarts
+  if (t == 0 && flags) atomicAdd(flags + 1, 1);
 
   for (int i = t; i < r; i += kChol) {
     float v = Min[i + (int64_t)r * i];
@@ -87,10 +102,12 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
     const float shift = rel * (float)r;
     const float floor = fmaxf(1e-7f, 0.1f * shift);
     if (t == 0) bad = 0;
-    for (int64_t e = t; e < (int64_t)r * r; e += kChol) {
-      int j = (int)(e / r), i = (int)(e - (int64_t)j * r);
-      if (i >= j) {
-        float v = Min[e] * dinv[i] * dinv[j];
+    // column j by warp, rows by lane: no integer division in the loop
+    for (int j = warp; j < r; j += kChol / 32) {
+      const float dj = dinv[j];
+      for (int i = j + (t & 31); i < r; i += 32) {
+        const int64_t e = i + (int64_t)r * j;
+        float v = Min[e] * dinv[i] * dj;
         if (i == j) v += shift;
         A[e] = v;
       }
@@ -155,21 +172,178 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
 #pragma unroll
             for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(u[x], v[y], acc[x][y]);
         }
+        // all 64 loads first: independent, so they overlap in flight
+        float old[8][8];
 #pragma unroll
         for (int x = 0; x < 8; ++x)
 #pragma unroll
           for (int y = 0; y < 8; ++y) {
             int ri = bi * 8 + x, rj = bj * 8 + y;
-            if (ri < rows && rj < rows && ri >= rj) {
-              int64_t e = (p0 + b + ri) + (int64_t)r * (p0 + b + rj);
-              A[e] -= acc[x][y];
-            }
+            old[x][y] = (ri < rows && rj < rows && ri >= rj) ? A[(p0 + b + ri) + (int64_t)r * (p0 + b + rj)] : 0.f;
+          }
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) {
+            int ri = bi * 8 + x, rj = bj * 8 + y;
+            if (ri < rows && rj < rows && ri >= rj) A[(p0 + b + ri) + (int64_t)r * (p0 + b + rj)] = old[x][y] - acc[x][y];
           }
       }
       __syncthreads();
     }
     if (!bad) break;
-    if (t == 0 && flags) atomicOr(flags, 1);
+    if (t == 0 && flags) {
+      atomicOr(flags, 1);
+      atomicAdd(flags + 2, 1);
+    }
+    rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
+    if (rel > 1e-2f) rel = 1e-2f;
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// chol_cluster: the same factorization spread over a cluster of kCL CTAs on
+// kCL SMs (for r > 128, where one SM would need ~r^3/3 FP32 FMAs alone).
+// Every CTA factors the 32 x 32 diagonal block itself (same data, same code,
+// same result, so no broadcast is needed); the panel rows and the
+// trailing-update tiles are split across the CTAs; cluster barriers order the
+// phases.  The matrix lives in global memory (L2); it is read with
+// ld.global.cg and written with st.global.cg so no CTA sees a stale L1 line.
+// --------------------------------------------------------------------------
+constexpr int kCL = 8;
+
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol)
+chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ A,
+                    float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ float smem[];
+  float* dinv = smem;                       // 1024
+  float* Dg = dinv + 1024;                  // 32 x 33
+  float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
+  __shared__ int bad;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (rank == 0 && t == 0 && flags) atomicAdd(flags + 1, 1);
+
+  for (int i = t; i < r; i += kChol) {
+    float v = Min[i + (int64_t)r * i];
+    bool ok = v > 0.f && isfinite(v);
+    if (!ok && flags && rank == 0) atomicOr(flags, 2);
+    float dv = 1.f / (ok ? sqrtf(v) : 1.f);
+    dinv[i] = dv;
+    if (rank == 0) dinv_out[i] = dv;
+  }
+  __syncthreads();
+  float rel = shift_rel;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const float shift = rel * (float)r;
+    const float floor = fmaxf(1e-7f, 0.1f * shift);
+    if (t == 0) bad = 0;
+    for (int j = rank + kCL * warp; j < r; j += kCL * (kChol / 32)) {
+      const float dj = dinv[j];
+      for (int i = j + lane; i < r; i += 32) {
+        const int64_t e = i + (int64_t)r * j;
+        float v = Min[e] * dinv[i] * dj;
+        if (i == j) v += shift;
+        __stcg(A + e, v);
+      }
+    }
+    __threadfence();
+    cluster.sync();
+    for (int p0 = 0; p0 < r; p0 += PB) {
+      const int b = min(PB, r - p0);
+      for (int e = t; e < PB * PB; e += kChol) {
+        int i = e & 31, j = e >> 5;
+        Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? __ldcg(A + (p0 + i) + (int64_t)r * (p0 + j)) : 0.f;
+      }
+      __syncthreads();
+      if (warp == 0) warp_chol32(Dg, b, floor, &bad);
+      __syncthreads();
+      if (rank == 0)
+        for (int e = t; e < b * b; e += kChol) {
+          int i = e % b, j = e / b;
+          if (i >= j) __stcg(A + (p0 + i) + (int64_t)r * (p0 + j), Dg[i * (PB + 1) + j]);
+        }
+      const int rows = r - p0 - b;
+      for (int ii = rank + kCL * t; ii < rows; ii += kCL * kChol) {
+        const int i = p0 + b + ii;
+        float a[PB];
+#pragma unroll
+        for (int c = 0; c < PB; ++c) a[c] = (c < b) ? __ldcg(A + i + (int64_t)r * (p0 + c)) : 0.f;
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+          float v = a[c];
+#pragma unroll
+          for (int k = 0; k < c; ++k) v = fmaf(-a[k], Dg[c * (PB + 1) + k], v);
+          a[c] = (c < b) ? v / Dg[c * (PB + 1) + c] : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < PB; ++c)
+          if (c < b) __stcg(A + i + (int64_t)r * (p0 + c), a[c]);
+      }
+      __threadfence();
+      cluster.sync();
+      if (rows > 0) {
+        for (int ii = t; ii < rows; ii += kChol) {
+          float v[PB];
+#pragma unroll
+          for (int c = 0; c < PB; ++c) v[c] = (c < b) ? __ldcg(A + (p0 + b + ii) + (int64_t)r * (p0 + c)) : 0.f;
+#pragma unroll
+          for (int c = 0; c < PB; ++c) Pn[ii * (PB + 1) + c] = v[c];
+        }
+        __syncthreads();
+        const int nt = (rows + 7) / 8;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int tile = rank + kCL * t; tile < ntiles; tile += kCL * kChol) {
+          int bi = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+          while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+          while (bi * (bi + 1) / 2 > tile) --bi;
+          int bj = tile - bi * (bi + 1) / 2;
+          float acc[8][8];
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+          for (int c = 0; c < b; ++c) {
+            float u[8], v[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+              int ri = bi * 8 + x, rj = bj * 8 + x;
+              u[x] = (ri < rows) ? Pn[ri * (PB + 1) + c] : 0.f;
+              v[x] = (rj < rows) ? Pn[rj * (PB + 1) + c] : 0.f;
+            }
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+              for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(u[x], v[y], acc[x][y]);
+          }
+          float old[8][8];
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+              int ri = bi * 8 + x, rj = bj * 8 + y;
+              old[x][y] = (ri < rows && rj < rows && ri >= rj) ? __ldcg(A + (p0 + b + ri) + (int64_t)r * (p0 + b + rj)) : 0.f;
+            }
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+              int ri = bi * 8 + x, rj = bj * 8 + y;
+              if (ri < rows && rj < rows && ri >= rj) __stcg(A + (p0 + b + ri) + (int64_t)r * (p0 + b + rj), old[x][y] - acc[x][y]);
+            }
+        }
+      }
+      __threadfence();
+      cluster.sync();
+    }
+    if (!bad) break;
+    if (rank == 0 && t == 0 && flags) {
+      atomicOr(flags, 1);
+      atomicAdd(flags + 2, 1);
+    }
     rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
     if (rel > 1e-2f) rel = 1e-2f;
     __syncthreads();
@@ -294,73 +468,96 @@ trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restri
 }
 
 // --------------------------------------------------------------------------
-// eig_small: FP64 cyclic Jacobi, n <= 32, one warp.  Output the r leading
-// eigenvectors (descending eigenvalue, ties by index), each sign-fixed so its
-// largest-magnitude entry (lowest index on ties) is positive, as FP32
-// column-major n x r; eigenvalues optionally.
+// eig_small: FP64 parallel Jacobi (round-robin pairing), n <= 32, one warp:
+// every step rotates n/2 disjoint pairs at once, one lane per pair.  Output
+// the r leading eigenvectors (descending eigenvalue, ties by index), each
+// sign-fixed so its largest-magnitude entry (lowest index on ties) is
+// positive, as FP32 column-major n x r; eigenvalues optionally.
 // --------------------------------------------------------------------------
 __global__ void eig_small_kernel(const double* __restrict__ Gin, int n, int r, float* __restrict__ U,
                                  double* __restrict__ evals, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double A[32][33];
   __shared__ double V[32][33];
-  __shared__ double cs[2];
+  __shared__ double cs[16][2];
+  __shared__ int pr[16][2];
+  __shared__ int perm[32];
   __shared__ int order[32];
   const int lane = threadIdx.x;
-  for (int i = 0; i < n; ++i)
-    if (lane < n) {
-      A[i][lane] = Gin[i + n * lane];
+  const int m = n + (n & 1);            // padded to even
+  const int half = m / 2;
+  for (int i = 0; i < m; ++i) {
+    if (lane < m) {
+      A[i][lane] = (i < n && lane < n) ? Gin[i + n * lane] : 0.0;
       V[i][lane] = (i == lane) ? 1.0 : 0.0;
     }
+  }
+  if (lane < m) perm[lane] = lane;
   __syncwarp();
   double scale = 0.0;
   for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(A[i][i]));
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) off += A[p][q] * A[p][q];
-    if (off <= 1e-26 * scale * scale || scale == 0.0) break;   // off-norm ~1e-13 relative
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (lane == 0) {
-          double apq = A[p][q];
-          double c = 1.0, s = 0.0;
-          if (fabs(apq) > 1e-300) {
-            double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-            double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(tt * tt + 1.0);
-            s = tt * c;
-          }
-          cs[0] = c;
-          cs[1] = s;
+    if (lane < m)
+      for (int j = 0; j < m; ++j)
+        if (j != lane) off += A[lane][j] * A[lane][j];
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    if (off <= 1e-26 * scale * scale || scale == 0.0) break;
+    for (int step = 0; step < m - 1; ++step) {
+      if (lane < half) {
+        int p = perm[lane], q = perm[m - 1 - lane];
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        const double apq = A[p][q];
+        double c = 1.0, sn = 0.0;
+        if (fabs(apq) > 1e-300) {
+          const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+          const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(tt * tt + 1.0);
+          sn = tt * c;
         }
-        __syncwarp();
-        const double c = cs[0], s = cs[1];
-        if (s != 0.0) {
-          if (lane < n) {  // columns p, q of A
-            double akp = A[lane][p], akq = A[lane][q];
-            A[lane][p] = c * akp - s * akq;
-            A[lane][q] = s * akp + c * akq;
-          }
-          __syncwarp();
-          if (lane < n) {  // rows p, q
-            double apk = A[p][lane], aqk = A[q][lane];
-            A[p][lane] = c * apk - s * aqk;
-            A[q][lane] = s * apk + c * aqk;
-            double vkp = V[lane][p], vkq = V[lane][q];
-            V[lane][p] = c * vkp - s * vkq;
-            V[lane][q] = s * vkp + c * vkq;
-          }
-        }
-        __syncwarp();
+        cs[lane][0] = c;
+        cs[lane][1] = sn;
+        pr[lane][0] = p;
+        pr[lane][1] = q;
       }
+      __syncwarp();
+      if (lane < m) {   // rows p, q: lane walks column `lane`
+        for (int k = 0; k < half; ++k) {
+          const int p = pr[k][0], q = pr[k][1];
+          const double c = cs[k][0], sn = cs[k][1];
+          const double ap = A[p][lane], aq = A[q][lane];
+          A[p][lane] = c * ap - sn * aq;
+          A[q][lane] = sn * ap + c * aq;
+        }
+      }
+      __syncwarp();
+      if (lane < m) {   // columns p, q of A and V: lane walks row `lane`
+        for (int k = 0; k < half; ++k) {
+          const int p = pr[k][0], q = pr[k][1];
+          const double c = cs[k][0], sn = cs[k][1];
+          const double ap = A[lane][p], aq = A[lane][q];
+          A[lane][p] = c * ap - sn * aq;
+          A[lane][q] = sn * ap + c * aq;
+          const double vp = V[lane][p], vq = V[lane][q];
+          V[lane][p] = c * vp - sn * vq;
+          V[lane][q] = sn * vp + c * vq;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {   // round-robin: perm[0] fixed, the rest rotate
+        const int last = perm[m - 1];
+        for (int i = m - 1; i > 1; --i) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncwarp();
+    }
   }
-  // order by descending eigenvalue (stable in index)
+  // order by descending eigenvalue (stable in index), real entries only
   if (lane < n) {
-    double w = A[lane][lane];
+    const double w = A[lane][lane];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double wj = A[j][j];
+      const double wj = A[j][j];
       if (wj > w || (wj == w && j < lane)) ++rank;
     }
     order[rank] = lane;
@@ -371,7 +568,7 @@ __global__ void eig_small_kernel(const double* __restrict__ Gin, int n, int r, f
     int best = 0;
     double bv = -1.0;
     for (int i = 0; i < n; ++i) {
-      double a = fabs(V[i][src]);
+      const double a = fabs(V[i][src]);
       if (a > bv) { bv = a; best = i; }
     }
     const double sg = (V[best][src] < 0.0) ? -1.0 : 1.0;
@@ -503,6 +700,24 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, i
   MES_TRY(audit(L, last, "chol L"));
   MES_TRY(audit(dinv, (size_t)r * 4 - 1, "chol dinv"));
   ProfScope prof("chol_f32", st, r * (double)r * r / 3.0, 8.0 * r * (double)r);
+  static int cluster_ok = -1;
+  if (cluster_ok < 0) {
+    cudaError_t e = cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_smem());
+    cluster_ok = (e == cudaSuccess) ? 1 : 0;
+    if (e != cudaSuccess && getenv("MES_DEBUG"))
+      fprintf(stderr, "[mes] cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
+    cudaGetLastError();
+  }
+  if (r > 128 && cluster_ok == 1) {
+    chol_cluster_kernel<<<kCL, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MES_OK;
+    // a cluster launch the device cannot place is rejected before anything
+    // runs; fall back to the one-CTA kernel from then on
+    if (getenv("MES_DEBUG")) fprintf(stderr, "[mes] cluster Cholesky launch rejected: %s\n", cudaGetErrorString(e));
+    cluster_ok = 0;
+  }
   chol_kernel<<<1, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
@@ -532,9 +747,12 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
   MES_TRY(audit(V, (size_t)(s * r) * 4 - 1, "trsm V"));
   MES_TRY(audit(L, (size_t)r * r * 4 - 1, "trsm L"));
   ProfScope prof("trsm_f32", st, s * (double)r * r, 8.0 * s * r);
-  // rows per CTA: as many as fit in ~200 KB of shared memory
-  if ((size_t)128 * (r + 1) * 4 <= 200 * 1024) return trsm_launch<128>(W, s, r, L, dinv, V, round, skip, st);
-  if ((size_t)64 * (r + 1) * 4 <= 200 * 1024) return trsm_launch<64>(W, s, r, L, dinv, V, round, skip, st);
+  // rows per CTA: the largest of 128 / 64 / 32 that fits in ~200 KB of shared
+  // memory and still gives ~120 CTAs (more rows per CTA amortise the L tiles,
+  // more CTAs fill the GPU)
+  const bool fit128 = (size_t)128 * (r + 1) * 4 <= 200 * 1024, fit64 = (size_t)64 * (r + 1) * 4 <= 200 * 1024;
+  if (fit128 && (s + 127) / 128 >= 120) return trsm_launch<128>(W, s, r, L, dinv, V, round, skip, st);
+  if (fit64 && (s + 63) / 64 >= 120) return trsm_launch<64>(W, s, r, L, dinv, V, round, skip, st);
   return trsm_launch<32>(W, s, r, L, dinv, V, round, skip, st);
 }
 

@@ -204,7 +204,9 @@ def test_eckart_young_order2(mes):
     rng = np.random.default_rng(8)
     A = rng.standard_normal((300, 40)) @ np.diag(np.logspace(0, -2, 40)) @ rng.standard_normal((40, 170))
     r = 12
-    res = _run(mes, A, (r, r), 6, 0.0, inner_iters=4)
+    # the gap sigma_12 / sigma_13 is only ~1.12: give the subspace iteration
+    # enough steps to reach the optimum to 1e-5
+    res = _run(mes, A, (r, r), 10, 0.0, inner_iters=4, init_iters=4)
     s = np.linalg.svd(A, compute_uv=False)
     fit_ey = 1.0 - np.sqrt(np.sum(s[r:] ** 2)) / np.linalg.norm(A)
     assert abs(float(res["fit"].cpu()) - fit_ey) / fit_ey < 1e-5
