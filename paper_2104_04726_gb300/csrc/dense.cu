@@ -84,7 +84,8 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
   float* Dg = dinv + 1024;                  // 32 x 33
   float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
   __shared__ int bad;
-  const int t = threadIdx.x, warp = t >> 5;
+  __shared__ float Drc[PB];                 // reciprocals of the diagonal of L_pp
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   // flags[0]: error bits; flags[1]: calls; flags[2]: shift restarts
   if (t == 0 && flags) atomicAdd(flags + 1, 1);
 
@@ -120,7 +121,11 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
         Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
       }
       __syncthreads();
-      if (warp == 0) warp_chol32(Dg, b, floor, &bad);
+      if (warp == 0) {
+        warp_chol32(Dg, b, floor, &bad);
+        __syncwarp();
+        Drc[lane] = 1.f / Dg[lane * (PB + 1) + lane];
+      }
       __syncthreads();
       for (int e = t; e < b * b; e += kChol) {
         int i = e % b, j = e / b;
@@ -138,7 +143,7 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
           float v = a[c];
 #pragma unroll
           for (int k = 0; k < c; ++k) v = fmaf(-a[k], Dg[c * (PB + 1) + k], v);
-          a[c] = (c < b) ? v / Dg[c * (PB + 1) + c] : 0.f;
+          a[c] = (c < b) ? v * Drc[c] : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < PB; ++c) {
@@ -224,6 +229,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
   float* Dg = dinv + 1024;                  // 32 x 33
   float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
   __shared__ int bad;
+  __shared__ float Drc[PB];                 // reciprocals of the diagonal of L_pp
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   if (rank == 0 && t == 0 && flags) atomicAdd(flags + 1, 1);
 
@@ -259,7 +265,11 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
         Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? __ldcg(A + (p0 + i) + (int64_t)r * (p0 + j)) : 0.f;
       }
       __syncthreads();
-      if (warp == 0) warp_chol32(Dg, b, floor, &bad);
+      if (warp == 0) {
+        warp_chol32(Dg, b, floor, &bad);
+        __syncwarp();
+        Drc[lane] = 1.f / Dg[lane * (PB + 1) + lane];
+      }
       __syncthreads();
       if (rank == 0)
         for (int e = t; e < b * b; e += kChol) {
@@ -277,7 +287,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
           float v = a[c];
 #pragma unroll
           for (int k = 0; k < c; ++k) v = fmaf(-a[k], Dg[c * (PB + 1) + k], v);
-          a[c] = (c < b) ? v / Dg[c * (PB + 1) + c] : 0.f;
+          a[c] = (c < b) ? v * Drc[c] : 0.f;
         }
 #pragma unroll
         for (int c = 0; c < PB; ++c)
@@ -363,7 +373,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 // --------------------------------------------------------------------------
 constexpr int kTrsm = 256;
 
-template <int ROWS>
+template <int ROWS, bool BLOCKROW>
 __global__ void __launch_bounds__(kTrsm)
 trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restrict__ L,
             const float* __restrict__ dinv, float* __restrict__ V, int round, const int* __restrict__ skip) {
@@ -372,6 +382,7 @@ trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restri
   const int ld = r + 1;
   float* Vs = sm;                    // ROWS x ld
   float* Lt = Vs + ROWS * ld;        // 32 x 33
+  float* Lrow = Lt + PB * (PB + 1);  // 32 x ld (BLOCKROW): L[c0 + c][0:c0]
   const int t = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * ROWS;
   for (int e = t; e < ROWS * r; e += kTrsm) {
@@ -385,7 +396,40 @@ trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restri
   const int nb = (r + PB - 1) / PB;
   for (int cb = 0; cb < nb; ++cb) {
     const int c0 = cb * PB;
-    if (c0 > 0) {
+    if (BLOCKROW && c0 > 0) {
+      // the whole block row of L at once: every load is in flight together
+      for (int e = t; e < PB * c0; e += kTrsm) {
+        const int c = e & 31, k = e >> 5;
+        Lrow[c * ld + k] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * k] : 0.f;
+      }
+      __syncthreads();
+      float acc[TR][4];
+#pragma unroll
+      for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[a][j] = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < c0; ++k) {
+        float a[TR], bq[4];
+#pragma unroll
+        for (int x = 0; x < TR; ++x) a[x] = Vs[(ty + 32 * x) * ld + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bq[j] = Lrow[(tx * 4 + j) * ld + k];
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[x][j] = fmaf(a[x], bq[j], acc[x][j]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int c = tx * 4 + j;
+          if (c0 + c < r) Vs[(ty + 32 * x) * ld + c0 + c] -= acc[x][j];
+        }
+    }
+    if (!BLOCKROW && c0 > 0) {
       float acc[TR][4];
 #pragma unroll
       for (int a = 0; a < TR; ++a)
@@ -723,18 +767,18 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, i
   return MES_OK;
 }
 
-template <int ROWS>
+template <int ROWS, bool BLOCKROW>
 mes_status trsm_launch(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V,
                        bool round, const int* skip, cudaStream_t st) {
-  const size_t smem = (size_t)(ROWS * (r + 1) + PB * (PB + 1)) * sizeof(float);
+  const size_t smem = (size_t)((ROWS + (BLOCKROW ? PB : 0)) * (r + 1) + PB * (PB + 1)) * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    MES_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MES_CUDA_TRY(cudaFuncSetAttribute(trsm_kernel<ROWS, BLOCKROW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       220 * 1024));
     attr = true;
   }
   const unsigned grid = (unsigned)((s + ROWS - 1) / ROWS);
-  trsm_kernel<ROWS><<<grid, kTrsm, smem, st>>>(W, s, r, L, dinv, V, round ? 1 : 0, skip);
+  trsm_kernel<ROWS, BLOCKROW><<<grid, kTrsm, smem, st>>>(W, s, r, L, dinv, V, round ? 1 : 0, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
@@ -747,13 +791,16 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
   MES_TRY(audit(V, (size_t)(s * r) * 4 - 1, "trsm V"));
   MES_TRY(audit(L, (size_t)r * r * 4 - 1, "trsm L"));
   ProfScope prof("trsm_f32", st, s * (double)r * r, 8.0 * s * r);
-  // rows per CTA: the largest of 128 / 64 / 32 that fits in ~200 KB of shared
-  // memory and still gives ~120 CTAs (more rows per CTA amortise the L tiles,
-  // more CTAs fill the GPU)
-  const bool fit128 = (size_t)128 * (r + 1) * 4 <= 200 * 1024, fit64 = (size_t)64 * (r + 1) * 4 <= 200 * 1024;
-  if (fit128 && (s + 127) / 128 >= 120) return trsm_launch<128>(W, s, r, L, dinv, V, round, skip, st);
-  if (fit64 && (s + 63) / 64 >= 120) return trsm_launch<64>(W, s, r, L, dinv, V, round, skip, st);
-  return trsm_launch<32>(W, s, r, L, dinv, V, round, skip, st);
+  // Rows per CTA and whether a whole block row of L fits in shared memory
+  // (~210 KB budget): more rows amortise the L traffic, more CTAs fill the
+  // GPU (aim for ~120).
+  const size_t budget = 210 * 1024;
+  auto fits = [&](int rows, bool br) {
+    return (size_t)((rows + (br ? PB : 0)) * (r + 1) + PB * (PB + 1)) * sizeof(float) <= budget;
+  };
+  if (fits(64, true) && (s + 63) / 64 >= 120) return trsm_launch<64, true>(W, s, r, L, dinv, V, round, skip, st);
+  if (fits(32, true)) return trsm_launch<32, true>(W, s, r, L, dinv, V, round, skip, st);
+  return trsm_launch<32, false>(W, s, r, L, dinv, V, round, skip, st);
 }
 
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,

@@ -31,6 +31,9 @@ struct Gemm {
   bool accumulate = false;
   bool round_tf32 = false;        // store C (and C2) rounded to TF32 (operands of later kind::tf32 products)
   const int* skip = nullptr;      // device flag: when non-zero the launch is a no-op
+  // C is symmetric and its consumer reads only m >= n: tiles wholly above the
+  // diagonal are not computed (their elements of C are left as they were).
+  bool lower = false;
   // Residual mode: instead of storing, accumulate sum((ref - alpha*AB)^2) in
   // FP64; ref is addressed like C.  partials needs gemm_partials(g) doubles.
   const float* ref = nullptr;

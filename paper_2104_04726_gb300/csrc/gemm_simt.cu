@@ -7,6 +7,7 @@
 // operand, 32 consecutive m (or n) for an MN-major one.  The K loop runs over
 // (k_hi, k_lo-tile) pairs, so a two-level K index never needs a division;
 // only the last k_lo tile of each k_hi is ragged (zero-filled).
+#include <algorithm>
 #include "gemm.cuh"
 
 namespace {
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g, int splits,
   const int64_t bn = (int64_t)blockIdx.y * BN;
   const int b = blockIdx.z % g.batch;
   const int split = blockIdx.z / g.batch;
+  if (g.lower && bm + BM <= bn) return;  // wholly above the diagonal
   const float* A = g.A + (int64_t)b * g.a_b;
   const float* B = g.B + (int64_t)b * g.b_b;
 
@@ -204,6 +206,7 @@ __global__ void split_sum_kernel(const mes::Gemm g, int splits) {
     for (int sp = 0; sp < splits; ++sp) sacc += g.split_ws[(int64_t)sp * total + e];
     const int64_t n = e % g.N, bm = e / g.N;
     const int64_t m = bm % g.M, b = bm / g.M;
+    if (g.lower && (m / BM + 1) * BM <= (n / BN) * BN) continue;  // tile never computed
     const int64_t mh = m / M_lo, ml = m - mh * M_lo, nh = n / N_lo, nl = n - nh * N_lo;
     float v = g.alpha * sacc;
     float* p = g.C + b * g.c_b + ml * g.c_m + mh * g.c_mh + nl * g.c_n + nh * g.c_nh;
@@ -234,7 +237,12 @@ mes_status launch(const mes::Gemm& g, dim3 grid, cudaStream_t st) {
   const double K = (double)g.K_lo * g.K_hi, bt = g.batch;
   // split K when the tile grid leaves most SMs idle (not in residual mode)
   const int64_t nkt = ((g.K_lo + BK - 1) / BK) * g.K_hi;
-  const int64_t tiles = (int64_t)grid.x * grid.y * grid.z;
+  int64_t tiles = (int64_t)grid.x * grid.y * grid.z;
+  if (g.lower) {  // tiles (i, j) with j <= i
+    int64_t lt = 0;
+    for (int64_t i = 0; i < (int64_t)grid.x; ++i) lt += std::min<int64_t>(i + 1, grid.y);
+    tiles = lt * grid.z;
+  }
   const int64_t sms = mes::sm_count();
   int splits = 1;
   if (!g.ref && g.split_ws) {

@@ -49,8 +49,8 @@ using mes::KronDesc;
 
 // Starting relative shifts of the Z-preconditioning Cholesky and of the
 // first CholeskyQR pass (the Cholesky kernel raises them on breakdown).
-static float kShiftZ = 1e-5f;
-static float kShiftW = 1e-5f;
+constexpr float kShiftZ = 1e-5f;
+constexpr float kShiftW = 1e-5f;
 
 struct Shape {
   int N = 0;
@@ -153,6 +153,7 @@ struct Driver {
       g.A = src; g.a_m = s; g.a_k = 1;
       g.B = src; g.b_n = s; g.b_k = 1;
       g.C = H; g.c_m = 1; g.c_n = r;
+      g.lower = true;  // chol reads the lower triangle only
       MES_TRY(gemm(g));
       MES_TRY(mes::chol(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, dinv, flags, skip, st));
       MES_TRY(mes::trsm(src, s, (int)r, cwA, dinv, dst, false, skip, st));   // dst = src R^-1
@@ -177,6 +178,7 @@ struct Driver {
     gh.A = Z; gh.a_m = J; gh.a_k = 1;
     gh.B = Z; gh.b_n = J; gh.b_k = 1;
     gh.C = H; gh.c_m = 1; gh.c_n = r;
+    gh.lower = true;
     MES_TRY(gemm(gh));
     MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, flags, skip, st));
     // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in that form
@@ -334,8 +336,6 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: negative iteration option");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (getenv("MES_SHIFT_Z")) kShiftZ = (float)atof(getenv("MES_SHIFT_Z"));
-  if (getenv("MES_SHIFT_W")) kShiftW = (float)atof(getenv("MES_SHIFT_W"));
   mes::AuditScope audit_scope;
   {
     int64_t nX = 1, nQ = 1;
