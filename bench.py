@@ -1,12 +1,17 @@
 """Benchmark of the Tucker-ALS coding path on GB300.
 
-One step = the whole path on one 1920x1080, 2-view x 5-exposure stack
-(paper dims 1920 x 1080 x 3 x 10, IPT, ranks (384, 256, 3, 10), 20 sweeps):
+One step = the whole path on a batch of 1920x1080, 2-view x 5-exposure stacks
+(dims 1920 x 1080 x 3 x 10, IPT, ranks (384, 256, 3, 10), 20 sweeps each):
 colour pre-pass of the resident 8-bit images, Tucker-ALS / HOOI, core
 quantiser (16 bits) and reconstruction with the fused residual.  The metric
 is stacks per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--precision tf32|fp32] [--stacks S] [--no-fp32-path]
+
+The default times the TF32 tensor-core form over 8 concurrent stacks per step
+and, beside it, the plain FP32 path on the same stacks (its stacks/s and the
+largest relative fit deviation between the two).
 
 Multi-GPU (torchrun, one rank per GPU): every rank decomposes its own stacks
 (independent problems, weak scaling, no collective on the data path); the
@@ -137,12 +142,22 @@ def cpu_baseline(sample_sweeps: int = 1):
             "seconds": t4 - t0}
 
 
+def _config(name, cfg, dims, ranks, precision, stacks, world):
+    return {"workload": name, "dims": dims, "ranks": ranks, "sweeps": cfg["iters"], "colour": cfg["space"],
+            "precision": precision, "quant_bits": 16, "stacks_per_step": stacks,
+            "l2": "inputs larger than L2 (each stack: 249 MB FP32 tensor + 249 MB second layout)",
+            "parallelism": f"stack-parallel x{world}"}
+
+
 def run_reference(args):
+    """The oracle timed on the host cores: one bounded sample of the workload
+    per step (rank 0 only)."""
+    import synth
     rank, world, _ = _dist_env()
     if rank != 0:
         return 0
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
+    for _ in range(args.warmup):
+        cpu_baseline(1)
     times = []
     last = None
     for _ in range(args.steps):
@@ -150,16 +165,77 @@ def run_reference(args):
         times.append(1.0 / last["value"])
     per = statistics.mean(times)
     val = 1.0 / per
+    cfg = synth.config_spec(args.workload)
+    spec = cfg["spec"]
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "stacks/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": [1920, 1080, 3, 10], "ranks": [384, 256, 3, 10],
-                       "sweeps": 20, "colour": "ipt"},
+            "config": _config(args.workload, cfg, [spec.s1, spec.s2, 3, spec.K], list(cfg["ranks"]),
+                              args.precision, args.stacks, world),
             "cpu_baseline": {"value": val, "unit": "stacks/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": val, "unit": "stacks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _traffic(family):
+    """DRAM bytes per launch of a kernel family from the committed ncu
+    summary, or None when the kernel's source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            parts = ln.split()
+            if len(parts) < 4 or parts[0] != family:
+                continue
+            src = os.path.join(ROOT, parts[1])
+            if not os.path.exists(src):
+                return None, "source missing"
+            with open(src, "rb") as g:
+                digest = hashlib.sha256(g.read()).hexdigest()[:12]
+            if digest != parts[2]:
+                return None, f"{parts[1]} changed since the capture"
+            return float(parts[3]), " ".join(parts[4:])
+    return None, None
+
+
+def _roofline(fams, peaks, peak_src, sms):
+    total_ms = sum(f["ms"] for f in fams) or 1.0
+    top = fams[0]
+    traffic, note = _traffic(top["name"])
+    per_launch = lambda x: x / max(top["launches"], 1)
+    if top["name"].startswith("gemm_tf32_tc") or top["name"].startswith("gemm_bf16_tc"):
+        # tensor-core product: TF32 peak = half the measured BF16 dense peak
+        # (nominal TF32:BF16 ratio 1:2); sustained figure (timed inside a long step)
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if "tf32" in top["name"] else 1.0)
+        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{peak_src} bf16_tflops_sustained x {'0.5 (tf32)' if 'tf32' in top['name'] else '1'}"}
+    elif top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
+        # CUDA-core FP32 arithmetic: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz')} MHz"}
+    else:
+        achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": traffic, "kernel": top["name"],
+                 "share": top["ms"] / total_ms, "launches": top["launches"],
+                 "avg_launch_us": 1e3 * top["ms"] / max(top["launches"], 1),
+                 "algorithmic_bytes_per_launch": per_launch(top["bytes"]),
+                 "algorithmic_flops_per_launch": per_launch(top["flops"])})
+    if note:
+        roof["traffic_note"] = note
+    return roof
 
 
 def main():
@@ -168,15 +244,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mes", choices=["mes", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "bf16", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-path", action="store_true",
+                    help="skip timing the plain FP32 path beside the chosen precision form")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--stacks", type=int, default=8, help="independent stacks per step, one CUDA stream each")
     args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
 
     import paper_2104_04726_gb300 as mes
@@ -228,12 +307,12 @@ def main():
             self.f_host = [torch.empty((r, s), dtype=torch.float32, pin_memory=True) for s, r in zip(dims, ranks)]
             self.fit_host = torch.empty((), dtype=torch.float64, pin_memory=True)
 
-        def run(self, e2e=False):
+        def run(self, precision, e2e=False):
             with torch.cuda.stream(self.stream):
                 if e2e:
                     self.rgb.copy_(self.rgb_host, non_blocking=True)
                 mes.colour_convert(self.rgb, cfg["space"], out=self.X, norm2=self.n2)
-                mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=args.precision,
+                mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=precision,
                                outputs=(self.core, self.facs, self.fit, self.itd, None))
                 q, sc = mes.quantize_core(self.core, ranks, 16)
                 mes.reconstruct(self.core, self.facs, dims, ranks, ref=self.X)
@@ -245,114 +324,102 @@ def main():
                     self.fit_host.copy_(self.fit, non_blocking=True)
 
     stacks = [Stack(i) for i in range(S)]
-    main = torch.cuda.current_stream()
+    main_stream = torch.cuda.current_stream()
 
-    def step(e2e=False):
+    def step(precision, e2e=False):
         start = torch.cuda.Event()
-        start.record(main)
+        start.record(main_stream)
         for st_ in stacks:
             st_.stream.wait_event(start)
-            st_.run(e2e)
+            st_.run(precision, e2e)
         for st_ in stacks:
-            main.wait_stream(st_.stream)
+            main_stream.wait_stream(st_.stream)
 
-    def timed(n, e2e=False):
+    def timed(n, precision, e2e=False):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(main)
+        a.record(main_stream)
         for _ in range(n):
-            step(e2e)
-        b.record(main)
+            step(precision, e2e)
+        b.record(main_stream)
         torch.cuda.synchronize()
         t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
         if dist is not None:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K steps of S stacks, device events, barrier + sync
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    ms_max = timed(args.steps)
-    clocks = sampler.stop()
     n_stacks = args.steps * S * world
-    value = n_stacks / (ms_max / 1e3)
 
-    # ---- per-kernel profile over K more steps (events on each launch stream)
-    lib.mes_profile_enable(1)
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    fams = []
-    for i in range(lib.mes_profile_count()):
-        nm = ctypes.create_string_buffer(64)
-        n = ctypes.c_int64()
-        t_ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _lib.check(lib.mes_profile_get(i, nm, 64, ctypes.byref(n), ctypes.byref(t_ms), ctypes.byref(fl),
-                                       ctypes.byref(by)), "mes_profile_get")
-        fams.append({"name": nm.value.decode(), "launches": n.value, "ms": t_ms.value, "flops": fl.value,
-                     "bytes": by.value})
-    lib.mes_profile_enable(0)
-    fams.sort(key=lambda f: -f["ms"])
-    total_ms = sum(f["ms"] for f in fams) or 1.0
-    launches = sum(f["launches"] for f in fams)
+    def measure(precision, detail):
+        for _ in range(args.warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        # timed region: K steps of S stacks, device events, barrier + sync
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        ms_max = timed(args.steps, precision)
+        clocks = sampler.stop()
+        fits = [float(s_.fit.item()) for s_ in stacks]
+        out = {"value": n_stacks / (ms_max / 1e3), "ms_per_step": ms_max / args.steps, "clocks": clocks,
+               "fit": fits[0], "fits": fits}
+        if not detail:
+            return out
+        # per-kernel profile over K more steps (events on each launch stream)
+        lib.mes_profile_enable(1)
+        for _ in range(args.steps):
+            step(precision)
+        torch.cuda.synchronize()
+        fams = []
+        for i in range(lib.mes_profile_count()):
+            nm = ctypes.create_string_buffer(64)
+            n = ctypes.c_int64()
+            t_ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _lib.check(lib.mes_profile_get(i, nm, 64, ctypes.byref(n), ctypes.byref(t_ms), ctypes.byref(fl),
+                                           ctypes.byref(by)), "mes_profile_get")
+            fams.append({"name": nm.value.decode(), "launches": n.value, "ms": t_ms.value, "flops": fl.value,
+                         "bytes": by.value})
+        lib.mes_profile_enable(0)
+        fams.sort(key=lambda f: -f["ms"])
+        out["fams"] = fams
+        out["launches_per_step"] = sum(f["launches"] for f in fams) // args.steps
+        # end to end through the public API with host buffers
+        step(precision, True)
+        torch.cuda.synchronize()
+        e2e_ms = timed(args.steps, precision, e2e=True)
+        out["e2e"] = n_stacks / (e2e_ms / 1e3)
+        return out
+
+    res = measure(args.precision, True)
+    fp32 = None
+    if args.precision != "fp32" and not args.no_fp32_path:
+        fp32 = measure("fp32", False)
 
     peaks, peak_src = _peaks()
-    top = fams[0]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if top["name"].startswith("gemm_tf32_tc") or top["name"].startswith("gemm_bf16_tc"):
-        # tensor-core product: TF32 peak = half the measured BF16 dense peak
-        # (nominal TF32:BF16 ratio 1:2); sustained figure (timed inside a long step)
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if "tf32" in top["name"] else 1.0)
-        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained x {'0.5 (tf32)' if 'tf32' in top['name'] else '1'}",
-                "share": top["ms"] / total_ms}
-    elif top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
-        # CUDA-core FP32 arithmetic: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
-        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: {sms} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz')} MHz",
-                "share": top["ms"] / total_ms}
-    else:
-        achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "share": top["ms"] / total_ms}
-
-    # ---- end to end through the public API with host buffers
+    roof = _roofline(res["fams"], peaks, peak_src, sms)
     h2d = S * stacks[0].rgb_host.numel()
     d2h = S * (stacks[0].q_host.numel() * 2 + P * 4 + sum(f.numel() * 4 for f in stacks[0].f_host) + 8)
-    step(True)
-    torch.cuda.synchronize()
-    e2e_ms = timed(args.steps, e2e=True)
-    e2e_val = n_stacks / (e2e_ms / 1e3)
-    fit = stacks[0].fit
-    ms_per_step = ms_max / args.steps
-    fit_val = float(fit.item())
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "stacks/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        line = {"metric": METRIC, "value": res["value"], "unit": "stacks/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
                 "data": "synthetic",
-                "config": {"workload": name, "dims": dims, "ranks": ranks, "sweeps": iters, "colour": cfg["space"],
-                           "precision": args.precision, "quant_bits": 16, "stacks_per_step": S,
-                           "l2": "inputs larger than L2 (stack 249 MB FP32 + second layout 249 MB per step)",
-                           "parallelism": f"stack-parallel x{world}"},
-                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
-                "e2e": {"value": e2e_val, "unit": "stacks/s", "h2d_bytes_per_step": int(h2d),
+                "config": _config(name, cfg, dims, ranks, args.precision, S, world),
+                "roofline": roof, "gpu_launches": int(res["launches_per_step"] * args.steps),
+                "clocks": res["clocks"],
+                "e2e": {"value": res["e2e"], "unit": "stacks/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "fit": fit_val,
-                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in f.items()} for f in fams[:8]]}
+                "fit": res["fit"],
+                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in f.items()}
+                            for f in res["fams"][:8]]}
+        if fp32 is not None:
+            dev_rel = max(abs(a - b) / abs(b) for a, b in zip(res["fits"], fp32["fits"]))
+            line["fp32_path"] = {"value": fp32["value"], "ms_per_step": fp32["ms_per_step"], "fit": fp32["fit"],
+                                 "speedup": res["value"] / fp32["value"], "max_rel_fit_dev": dev_rel,
+                                 "clocks": fp32["clocks"]}
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
