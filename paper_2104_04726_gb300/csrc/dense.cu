@@ -65,6 +65,25 @@ __device__ __forceinline__ void chol_step(float (&row)[PB], int lane, int b, flo
   }
 }
 
+// Inverse of a 32 x 32 lower-triangular block held in shared memory with row
+// stride 33: lane j computes column j of L^-1 by forward substitution (the
+// rows of L are read as broadcasts); stored row-major to out[i * 32 + j].
+__device__ __forceinline__ void warp_tri_inv32(const float* Ls, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  float x[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i) x[i] = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+  for (int i = 0; i < PB; ++i) {
+    const float xi = x[i] / Ls[i * (PB + 1) + i];
+    x[i] = xi;
+#pragma unroll
+    for (int m = i + 1; m < PB; ++m) x[m] = fmaf(-Ls[m * (PB + 1) + i], xi, x[m]);
+  }
+#pragma unroll
+  for (int i = 0; i < PB; ++i) out[i * PB + lane] = x[i];
+}
+
 __device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad) {
   const int lane = threadIdx.x & 31;
   float row[PB];
@@ -361,14 +380,239 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 }
 
 // --------------------------------------------------------------------------
+// chol_dsm: the factorization for 128 < r <= 512 with the whole matrix in the
+// shared memory of a cluster of kCL CTAs, so no phase goes through L2.
+// Block column k (rows 32k .. rp-1, rp = r rounded up to 32; rows at and
+// beyond r are zero) lives in CTA k mod kCL, row-major with stride 33.
+// Step p: every CTA that owns a column right of p copies the rows of panel
+// p it needs from the owner's shared memory (distributed shared memory); the
+// owner of column p + 1 applies panel p to that column first, factors its
+// diagonal block in registers and solves its panel (look-ahead), then every
+// CTA applies panel p to the rest of its columns.  One cluster barrier per
+// step; a bad pivot is reported to CTA 0's flag for the attempt and every
+// CTA reads it after the same barrier, so all restart together.
+// --------------------------------------------------------------------------
+constexpr int kDsmMaxR = 512;
+constexpr int LD = PB + 1;
+
+__device__ __forceinline__ int dsm_slot_offset(int rank, int slot, int rp) {
+  int off = 0;
+  for (int q = 0; q < slot; ++q) off += rp - PB * (rank + kCL * q);
+  return off;  // rows
+}
+
+__host__ __device__ inline size_t chol_dsm_smem(int r) {
+  const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
+  int rows = 0;  // CTA 0 holds the most rows
+  for (int k = 0; k < nb; k += kCL) rows += rp - PB * k;
+  return (size_t)((rows + rp) * LD + rp) * sizeof(float);
+}
+
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol)
+chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
+                float* __restrict__ dinv_out, float* __restrict__ Linv_blk, int* __restrict__ flags,
+                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
+  extern __shared__ float smem[];
+  float* dinv = smem;              // rp
+  float* store = dinv + rp;        // owned block columns
+  int store_rows = 0;
+  for (int k = rank; k < nb; k += kCL) store_rows += rp - PB * k;
+  float* Pl = store + store_rows * LD;  // copied panel rows
+  // bad-pivot flags per attempt and step parity; CTA 0's copy is the
+  // cluster's.  A factor in step p reports to [p & 1]; the flag is read at the
+  // top of step p + 1, before anyone can reach step p + 2 and write that
+  // parity again, so every CTA reads the same value.
+  __shared__ int badv[8][2];
+  __shared__ int lbad;
+  __shared__ float Drc[PB];
+  if (t < 16) badv[t >> 1][t & 1] = 0;
+  if (rank == 0 && t == 0 && flags) atomicAdd(flags + 1, 1);
+  for (int i = t; i < rp; i += kChol) {
+    float dv = 0.f;
+    if (i < r) {
+      const float v = Min[i + (int64_t)r * i];
+      const bool ok = v > 0.f && isfinite(v);
+      if (!ok && flags && rank == 0) atomicOr(flags, 2);
+      dv = 1.f / (ok ? sqrtf(v) : 1.f);
+      if (rank == 0) dinv_out[i] = dv;
+    }
+    dinv[i] = dv;
+  }
+  volatile int* bad0 = cluster.map_shared_rank(&badv[0][0], 0);
+  cluster.sync();  // every badv zeroed before anyone can report
+
+  // the owner factors its column k: 32 x 32 diagonal block in registers by
+  // warp 0, then the rows below by forward substitution (one row a thread)
+  auto factor_col = [&](float* Sk, int k, float floor) {
+    const int b = min(PB, r - PB * k);
+    if (warp == 0) {
+      warp_chol32(Sk, b, floor, &lbad);
+      __syncwarp();
+      Drc[lane] = 1.f / Sk[lane * LD + lane];
+    }
+    __syncthreads();
+    const int h = rp - PB * k;
+    for (int i = PB + t; i < h; i += kChol) {
+      float a[PB];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) a[c] = Sk[i * LD + c];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        const float x = a[c] * Drc[c];
+        a[c] = x;
+#pragma unroll
+        for (int j = c + 1; j < PB; ++j) a[j] = fmaf(-x, Sk[j * LD + c], a[j]);
+      }
+#pragma unroll
+      for (int c = 0; c < PB; ++c) Sk[i * LD + c] = a[c];
+    }
+  };
+  // apply the copied panel (rows g_lo .. rp-1 in Pl) to owned column k:
+  // warp items of 128 rows x 4 columns, lane = row (+32 x), 4 x 4 registers
+  auto update_col = [&](float* Sk, int k, int g_lo) {
+    const int h = rp - PB * k;
+    const int items = ((h + 127) / 128) * 8;
+    const float* prow = Pl + (PB * k - g_lo) * LD;
+    for (int it = warp; it < items; it += kChol / 32) {
+      const int i0 = (it >> 3) * 128 + lane, c0 = (it & 7) * 4;
+      const float* pc = prow + c0 * LD;
+      float acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 8
+      for (int q = 0; q < PB; ++q) {
+        float u[4], v[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) u[x] = (i0 + 32 * x < h) ? prow[(i0 + 32 * x) * LD + q] : 0.f;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) v[y] = pc[y * LD + q];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(u[x], v[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int i = i0 + 32 * x;
+        if (i < h)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) Sk[i * LD + c0 + y] -= acc[x][y];
+      }
+    }
+  };
+
+  float rel = shift_rel;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const float shift = rel * (float)r;
+    const float floor = fmaxf(1e-7f, 0.1f * shift);
+    if (t == 0) lbad = 0;
+    // owned columns of A = D^-1 M D^-1 + shift I (lower part; rows >= r zero)
+    for (int k = rank, off = 0; k < nb; off += rp - PB * k, k += kCL) {
+      const int h = rp - PB * k;
+      float* Sk = store + off * LD;
+      for (int e = t; e < h * PB; e += kChol) {
+        const int i = e % h, c = e / h;
+        const int g = PB * k + i, j = PB * k + c;
+        float v = 0.f;
+        if (g < r && j < r && g >= j) {
+          v = Min[g + (int64_t)r * j] * dinv[g] * dinv[j];
+          if (g == j) v += shift;
+        }
+        Sk[i * LD + c] = v;
+      }
+    }
+    __syncthreads();
+    if (rank == 0) {
+      factor_col(store, 0, floor);
+      __syncthreads();
+      if (t == 0 && lbad) bad0[2 * attempt + 1] = 1;  // step -1
+    }
+    cluster.sync();
+    bool failed = false;
+    for (int p = 0; p < nb - 1; ++p) {
+      if (bad0[2 * attempt + ((p - 1) & 1)]) { failed = true; break; }
+      int kmin = rank;
+      while (kmin <= p) kmin += kCL;
+      if (kmin < nb) {
+        const int owner = p % kCL, g_lo = PB * kmin;
+        const float* src = cluster.map_shared_rank(store, owner) +
+                           (dsm_slot_offset(owner, p / kCL, rp) + (g_lo - PB * p)) * LD;
+        const int n = (rp - g_lo) * LD;
+        for (int e = t; e < n; e += kChol) Pl[e] = src[e];
+        __syncthreads();
+        int slot = (kmin - rank) / kCL;
+        int off = dsm_slot_offset(rank, slot, rp);
+        if (kmin == p + 1) {  // look-ahead: next panel first
+          float* Sk = store + off * LD;
+          update_col(Sk, kmin, g_lo);
+          __syncthreads();
+          factor_col(Sk, kmin, floor);
+          __syncthreads();
+          if (t == 0 && lbad) bad0[2 * attempt + (p & 1)] = 1;
+          off += rp - PB * kmin;
+          kmin += kCL;
+        }
+        for (int k = kmin; k < nb; off += rp - PB * k, k += kCL) update_col(store + off * LD, k, g_lo);
+      }
+      cluster.sync();
+    }
+    if (!failed && nb >= 2 && bad0[2 * attempt + ((nb - 2) & 1)]) failed = true;
+    if (!failed) break;
+    if (rank == 0 && t == 0 && flags) {
+      atomicOr(flags, 1);
+      atomicAdd(flags + 2, 1);
+    }
+    rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
+    if (rel > 1e-2f) rel = 1e-2f;
+    cluster.sync();
+  }
+  // L (lower triangle, column-major) and the inverses of the owned diagonal
+  // blocks (one warp each)
+  for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += kCL, ++q) {
+    const int h = rp - PB * k;
+    const float* Sk = store + off * LD;
+    if (warp == q) warp_tri_inv32(Sk, Linv_blk + (size_t)k * PB * PB);
+    for (int e = t; e < h * PB; e += kChol) {
+      const int i = e % h, c = e / h;
+      const int g = PB * k + i, j = PB * k + c;
+      if (g < r && j < r && g >= j) Lout[g + (int64_t)r * j] = Sk[i * LD + c];
+    }
+  }
+}
+
+// Inverses of the diagonal 32 x 32 blocks of L (global, column-major), one
+// warp per block: for the factorizations that do not produce them.
+__global__ void diag_inv_kernel(const float* __restrict__ L, int r, float* __restrict__ Linv_blk,
+                                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float Ls[4][PB * (PB + 1)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 4 + warp;
+  const int nb = (r + PB - 1) / PB;
+  if (k >= nb) return;
+  const int b = min(PB, r - PB * k);
+  for (int c = 0; c < PB; ++c)
+    Ls[warp][lane * (PB + 1) + c] =
+        (lane < b && c < b) ? (c <= lane ? L[(PB * k + lane) + (int64_t)r * (PB * k + c)] : 0.f) : (c == lane ? 1.f : 0.f);
+  __syncwarp();
+  warp_tri_inv32(Ls[warp], Linv_blk + (size_t)k * PB * PB);
+}
+
+// --------------------------------------------------------------------------
 // trsm: V = W D^-1 L^-T for an s x r column-major W (rows independent), i.e.
 // W * Rinv with Rinv = D^-1 L^-T, without forming Rinv.  ROWS rows per CTA
 // live in shared memory; column blocks of 32 in order:
-//   1. subtract the solved blocks times L: a ROWS x 32 x c0 product, 4 x 4
-//      register tiles, L staged in 32 x 32 tiles (next tile prefetched into
-//      registers while the current one is used);
-//   2. forward substitution with the 32 x 32 diagonal block of L, one row
-//      per thread.
+//   1. subtract the solved blocks times L: a ROWS x 32 x c0 product, 4-column
+//      register tiles, the block row of L staged in shared memory;
+//   2. multiply by the inverse of the 32 x 32 diagonal block (computed with
+//      the factorization): a ROWS x 32 x 32 product, no serial chain.
 // With `round`, V is stored rounded to TF32 (an operand of kind::tf32).
 // --------------------------------------------------------------------------
 constexpr int kTrsm = 256;
@@ -376,7 +620,8 @@ constexpr int kTrsm = 256;
 template <int ROWS, bool BLOCKROW>
 __global__ void __launch_bounds__(kTrsm)
 trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restrict__ L,
-            const float* __restrict__ dinv, float* __restrict__ V, int round, const int* __restrict__ skip) {
+            const float* __restrict__ dinv, const float* __restrict__ Linv_blk, float* __restrict__ V, int round,
+            const int* __restrict__ skip) {
   if (skip && *skip) return;
   extern __shared__ float sm[];
   const int ld = r + 1;
@@ -478,26 +723,38 @@ trsm_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restri
           if (c0 + c < r) Vs[(ty + 32 * x) * ld + c0 + c] -= acc[x][j];
         }
     }
-    // diagonal block of L into Lt (Lt[c][k] = L[c0 + c][c0 + k])
+    // x_blk := x_blk Linv^T with Linv = (L_cb,cb)^-1 staged as Lt[c][k]
     for (int e = t; e < PB * PB; e += kTrsm) {
-      int c = e & 31, k = e >> 5;
-      Lt[c * (PB + 1) + k] = (c0 + c < r && c0 + k < r) ? L[(c0 + c) + (int64_t)r * (c0 + k)] : (c == k ? 1.f : 0.f);
+      const int c = e >> 5, k = e & 31;
+      Lt[c * (PB + 1) + k] = Linv_blk[(size_t)cb * PB * PB + c * PB + k];
     }
     __syncthreads();
-    for (int i = t; i < ROWS; i += kTrsm) {
-      float x[PB];
+    {
+      float acc[TR][4];
 #pragma unroll
-      for (int c = 0; c < PB; ++c) x[c] = (c0 + c < r) ? Vs[i * ld + c0 + c] : 0.f;
+      for (int a = 0; a < TR; ++a)
 #pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        float v = x[c];
+        for (int j = 0; j < 4; ++j) acc[a][j] = 0.f;
+      const int kmax = min(PB, r - c0);
+      for (int k = 0; k < kmax; ++k) {
+        float a[TR], bq[4];
 #pragma unroll
-        for (int k = 0; k < c; ++k) v = fmaf(-x[k], Lt[c * (PB + 1) + k], v);
-        x[c] = v / Lt[c * (PB + 1) + c];
+        for (int x = 0; x < TR; ++x) a[x] = Vs[(ty + 32 * x) * ld + c0 + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bq[j] = Lt[(tx * 4 + j) * (PB + 1) + k];
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[x][j] = fmaf(a[x], bq[j], acc[x][j]);
       }
+      __syncthreads();
 #pragma unroll
-      for (int c = 0; c < PB; ++c)
-        if (c0 + c < r) Vs[i * ld + c0 + c] = x[c];
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = tx * 4 + j;
+          if (c0 + c < r) Vs[(ty + 32 * x) * ld + c0 + c] = acc[x][j];
+        }
     }
     __syncthreads();
   }
@@ -728,10 +985,17 @@ eig_mid_kernel(const float* __restrict__ Hin, int r, float* __restrict__ Z, cons
 
 namespace mes {
 
+static mes_status diag_inv(const float* L, int r, float* Linv_blk, const int* skip, cudaStream_t st) {
+  const int nb = (r + PB - 1) / PB;
+  diag_inv_kernel<<<(nb + 3) / 4, 128, 0, st>>>(L, r, Linv_blk, skip);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
 size_t chol_smem() { return (1024 + PB * (PB + 1) + 1024 * (PB + 1)) * sizeof(float); }
 
-mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, int* flags, const int* skip,
-                cudaStream_t st) {
+mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, float* Linv_blk, int* flags,
+                const int* skip, cudaStream_t st) {
   if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "chol: rank above 1024");
   static bool attr = false;
   if (!attr) {
@@ -743,6 +1007,7 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, i
   MES_TRY(audit(M, last, "chol M"));
   MES_TRY(audit(L, last, "chol L"));
   MES_TRY(audit(dinv, (size_t)r * 4 - 1, "chol dinv"));
+  MES_TRY(audit(Linv_blk, (size_t)((r + PB - 1) / PB) * PB * PB * 4 - 1, "chol Linv blocks"));
   ProfScope prof("chol_f32", st, r * (double)r * r / 3.0, 8.0 * r * (double)r);
   static int cluster_ok = -1;
   if (cluster_ok < 0) {
@@ -753,10 +1018,27 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, i
       fprintf(stderr, "[mes] cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
     cudaGetLastError();
   }
+  static int dsm_ok = -1;
+  if (dsm_ok < 0) {
+    cudaError_t e = cudaFuncSetAttribute(chol_dsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_dsm_smem(kDsmMaxR));
+    dsm_ok = (e == cudaSuccess) ? 1 : 0;
+    if (e != cudaSuccess && getenv("MES_DEBUG"))
+      fprintf(stderr, "[mes] shared-memory cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
+    cudaGetLastError();
+  }
+  if (r > 128 && r <= kDsmMaxR && dsm_ok == 1) {
+    chol_dsm_kernel<<<kCL, kChol, chol_dsm_smem(r), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MES_OK;
+    if (getenv("MES_DEBUG"))
+      fprintf(stderr, "[mes] shared-memory cluster Cholesky launch rejected: %s\n", cudaGetErrorString(e));
+    dsm_ok = 0;
+  }
   if (r > 128 && cluster_ok == 1) {
     chol_cluster_kernel<<<kCL, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) return MES_OK;
+    if (e == cudaSuccess) return diag_inv(L, r, Linv_blk, skip, st);
     // a cluster launch the device cannot place is rejected before anything
     // runs; fall back to the one-CTA kernel from then on
     if (getenv("MES_DEBUG")) fprintf(stderr, "[mes] cluster Cholesky launch rejected: %s\n", cudaGetErrorString(e));
@@ -764,12 +1046,12 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, i
   }
   chol_kernel<<<1, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
   MES_LAUNCH_CHECK();
-  return MES_OK;
+  return diag_inv(L, r, Linv_blk, skip, st);
 }
 
 template <int ROWS, bool BLOCKROW>
-mes_status trsm_launch(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V,
-                       bool round, const int* skip, cudaStream_t st) {
+mes_status trsm_launch(const float* W, int64_t s, int r, const float* L, const float* dinv, const float* Linv_blk,
+                       float* V, bool round, const int* skip, cudaStream_t st) {
   const size_t smem = (size_t)((ROWS + (BLOCKROW ? PB : 0)) * (r + 1) + PB * (PB + 1)) * sizeof(float);
   static bool attr = false;
   if (!attr) {
@@ -778,18 +1060,19 @@ mes_status trsm_launch(const float* W, int64_t s, int r, const float* L, const f
     attr = true;
   }
   const unsigned grid = (unsigned)((s + ROWS - 1) / ROWS);
-  trsm_kernel<ROWS, BLOCKROW><<<grid, kTrsm, smem, st>>>(W, s, r, L, dinv, V, round ? 1 : 0, skip);
+  trsm_kernel<ROWS, BLOCKROW><<<grid, kTrsm, smem, st>>>(W, s, r, L, dinv, Linv_blk, V, round ? 1 : 0, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
 
-mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V, bool round,
-                const int* skip, cudaStream_t st) {
+mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, const float* Linv_blk, float* V,
+                bool round, const int* skip, cudaStream_t st) {
   if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "trsm: rank above 1024");
   if (W == V) return fail(MES_ERR_INVALID_ARG, "trsm: in-place solve not supported");
   MES_TRY(audit(W, (size_t)(s * r) * 4 - 1, "trsm W"));
   MES_TRY(audit(V, (size_t)(s * r) * 4 - 1, "trsm V"));
   MES_TRY(audit(L, (size_t)r * r * 4 - 1, "trsm L"));
+  MES_TRY(audit(Linv_blk, (size_t)((r + PB - 1) / PB) * PB * PB * 4 - 1, "trsm Linv blocks"));
   ProfScope prof("trsm_f32", st, s * (double)r * r, 8.0 * s * r);
   // Rows per CTA and whether a whole block row of L fits in shared memory
   // (~210 KB budget): more rows amortise the L traffic, more CTAs fill the
@@ -798,9 +1081,9 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
   auto fits = [&](int rows, bool br) {
     return (size_t)((rows + (br ? PB : 0)) * (r + 1) + PB * (PB + 1)) * sizeof(float) <= budget;
   };
-  if (fits(64, true) && (s + 63) / 64 >= 120) return trsm_launch<64, true>(W, s, r, L, dinv, V, round, skip, st);
-  if (fits(32, true)) return trsm_launch<32, true>(W, s, r, L, dinv, V, round, skip, st);
-  return trsm_launch<32, false>(W, s, r, L, dinv, V, round, skip, st);
+  if (fits(64, true) && (s + 63) / 64 >= 120) return trsm_launch<64, true>(W, s, r, L, dinv, Linv_blk, V, round, skip, st);
+  if (fits(32, true)) return trsm_launch<32, true>(W, s, r, L, dinv, Linv_blk, V, round, skip, st);
+  return trsm_launch<32, false>(W, s, r, L, dinv, Linv_blk, V, round, skip, st);
 }
 
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,

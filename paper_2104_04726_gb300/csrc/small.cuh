@@ -56,12 +56,13 @@ mes_status permute_core(const float* in, int64_t total, int64_t stride, int r, c
                         const float* sign, float* out, cudaStream_t st);
 
 // dense.cu
-// Shifted Cholesky of an r x r Gram (L, dinv, inverted diagonal blocks) and
+// Shifted Cholesky of an r x r Gram: L, dinv and the inverses of the 32 x 32
+// diagonal blocks of L (Linv_blk: ceil(r/32) row-major 32 x 32 blocks), and
 // the right-side solve V = W D^-1 L^-T that completes one CholeskyQR pass.
-mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, int* flags, const int* skip,
-                cudaStream_t st);
-mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, float* V, bool round,
+mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, float* Linv_blk, int* flags,
                 const int* skip, cudaStream_t st);
+mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, const float* Linv_blk,
+                float* V, bool round, const int* skip, cudaStream_t st);
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,
                      cudaStream_t st);
 mes_status eig_mid(const float* H, int r, float* Z, const int* skip, cudaStream_t st);

@@ -113,6 +113,7 @@ struct Driver {
 
   float *cwA = nullptr, *cwX = nullptr, *H = nullptr, *Rinv = nullptr;
   float* dinv = nullptr;                    // equilibration of chol
+  float* linv = nullptr;                    // inverted diagonal blocks of L
   float *W = nullptr, *W2 = nullptr, *Z = nullptr, *Zh = nullptr, *Kmat = nullptr;
   double *gpart = nullptr, *G64 = nullptr;
 
@@ -155,8 +156,8 @@ struct Driver {
       g.C = H; g.c_m = 1; g.c_n = r;
       g.lower = true;  // chol reads the lower triangle only
       MES_TRY(gemm(g));
-      MES_TRY(mes::chol(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, dinv, flags, skip, st));
-      MES_TRY(mes::trsm(src, s, (int)r, cwA, dinv, dst, false, skip, st));   // dst = src R^-1
+      MES_TRY(mes::chol(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, dinv, linv, flags, skip, st));
+      MES_TRY(mes::trsm(src, s, (int)r, cwA, dinv, linv, dst, false, skip, st));   // dst = src R^-1
       src = dst;
     }
     if (prec == MES_PREC_TF32 && Srnd) MES_TRY(mes::round_copy(Sout, Srnd, s * r, skip, st));
@@ -180,9 +181,9 @@ struct Driver {
     gh.C = H; gh.c_m = 1; gh.c_n = r;
     gh.lower = true;
     MES_TRY(gemm(gh));
-    MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, flags, skip, st));
+    MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, linv, flags, skip, st));
     // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in that form
-    MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, Zh, prec == MES_PREC_TF32, skip, st));
+    MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, linv, Zh, prec == MES_PREC_TF32, skip, st));
     // W = Y Zh   (s x r)
     Gemm gw = wdesc;
     gw.C = W; gw.c_m = 1; gw.c_n = s;
@@ -307,15 +308,18 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
 
 }  // namespace
 
-extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
-                                     int max_iters, double tol, float* core, float* const* factors,
-                                     double* fit, const mes_als_opts* opts, void* stream) {
-  mes::clear_error();
+// The decomposition; with ws_bytes non-null only the workspace it would take
+// from the stream-ordered allocator is computed (no pointer is used).
+static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, const int64_t* ranks,
+                                  int max_iters, double tol, float* core, float* const* factors,
+                                  double* fit, const mes_als_opts* opts, void* stream, size_t* ws_bytes) {
   Shape sh;
   MES_TRY(make_shape(N, dims, ranks, &sh, "mes_tucker_als"));
-  if (!X || !core || !factors) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: null pointer");
-  for (int n = 0; n < N; ++n)
-    if (!factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: factors[%d] is null", n);
+  if (!ws_bytes) {
+    if (!X || !core || !factors) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: null pointer");
+    for (int n = 0; n < N; ++n)
+      if (!factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: factors[%d] is null", n);
+  }
   if (max_iters < 1) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: max_iters must be >= 1");
   if (!(tol >= 0.0)) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: tol must be >= 0");
   mes_als_opts o;
@@ -337,14 +341,14 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
-  {
+  if (!ws_bytes) {
     int64_t nX = 1, nQ = 1;
     for (int n = 0; n < N; ++n) { nX *= sh.s[n]; nQ *= sh.r[n]; }
     mes::audit_register(X, (size_t)nX * 4);
     mes::audit_register(core, (size_t)nQ * 4);
     for (int n = 0; n < N; ++n) mes::audit_register(factors[n], (size_t)(sh.s[n] * sh.r[n]) * 4);
   }
-  mes::Scratch scr(st);
+  mes::Scratch scr(st, ws_bytes != nullptr);
   Driver d;
   d.sh = sh;
   d.st = st;
@@ -400,6 +404,7 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   MES_TRY(scr.alloc(&d.cwA, rmax * rmax));
   MES_TRY(scr.alloc(&d.cwX, rmax * rmax));
   MES_TRY(scr.alloc(&d.dinv, rmax));
+  MES_TRY(scr.alloc(&d.linv, (rmax + 31) / 32 * 1024));
   MES_TRY(scr.alloc(&d.Kmat, 16384));
   MES_TRY(scr.alloc(&d.gpart, (size_t)mes::small_gram_blocks(s1 * s2) * 1024));
   MES_TRY(scr.alloc(&d.G64, 1024));
@@ -414,6 +419,10 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
   MES_TRY(scr.alloc(&sign, rmax));
   MES_TRY(scr.alloc(&order, rmax));
   d.flags = flags;
+  if (ws_bytes) {
+    *ws_bytes = scr.total;
+    return MES_OK;
+  }
   MES_CUDA_TRY(cudaMemsetAsync(done, 0, 8 * sizeof(int), st));
   if (o.iters_done) MES_CUDA_TRY(cudaMemsetAsync(o.iters_done, 0, sizeof(int), st));
 
@@ -480,6 +489,34 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
 
   // ---- sweeps (Eq. 8), n = 1..N ----
   d.skip = done;
+  // factor of small mode n from the Gram of B x_{m != n, m >= 3} S_m^T
+  auto small_mode_update = [&](int n) -> mes_status {
+    KronDesc kd;
+    kd.nm = sh.nsm;
+    for (int m = 0; m < sh.nsm; ++m) {
+      kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2];
+      kd.op[m] = (m + 2 == n) ? 'I' : 'T';
+      kd.U[m] = factors[m + 2];
+    }
+    Fibres fb;
+    fb.F_lo = r1; fb.F_hi = r2;
+    fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
+    return d.small_update(fb, kd, n - 2, factors[n]);
+  };
+  // core = B x_{n>=3} S_n^T
+  auto core_from_B = [&](const int* skipf) -> mes_status {
+    KronDesc kd;
+    kd.nm = sh.nsm;
+    for (int m = 0; m < sh.nsm; ++m) {
+      kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'T'; kd.U[m] = factors[m + 2];
+    }
+    MES_TRY(mes::kron_build(kd, d.Kmat, skipf, st));
+    Fibres fb;
+    fb.F_lo = r1; fb.F_hi = r2;
+    fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
+    fb.out = core; fb.out_lo = 1; fb.out_hi = r1; fb.out_l = r1 * r2;
+    return mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, skipf, st);
+  };
   for (int sweep = 1; sweep <= max_iters; ++sweep) {
     // mode 1: P = T x_2 S2^T, per l: P[x][q2 + r2 l] = sum_y XB[y + s2 x + s1 s2 l] U1[y + s2 q2]
     {
@@ -568,39 +605,32 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
       g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
       MES_TRY(d.big(g));
     }
-    // small modes n = 3..N: Gram of B x_{m != n} S_m^T, exact eigenvectors
-    for (int n = 2; n < N; ++n) {
-      KronDesc kd;
-      kd.nm = sh.nsm;
-      for (int m = 0; m < sh.nsm; ++m) {
-        kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2];
-        kd.op[m] = (m + 2 == n) ? 'I' : 'T';
-        kd.U[m] = factors[m + 2];
-      }
-      Fibres fb;
-      fb.F_lo = r1; fb.F_hi = r2;
-      fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
-      MES_TRY(d.small_update(fb, kd, n - 2, factors[n]));
-    }
+    // small modes n = 3..N with r_n < s_n: Gram of B x_{m != n} S_m^T, exact
+    // eigenvectors.  A full-rank small mode's factor is orthogonal: it leaves
+    // every other mode's Gram and the core norm unchanged, so its
+    // eigenvectors are taken once, after the last sweep.
+    for (int n = 2; n < N; ++n)
+      if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n));
     // core Q = B x_{n>=3} S_n^T (Eq. 5 / Eq. 7 with the current factors)
     {
-      KronDesc kd;
-      kd.nm = sh.nsm;
-      for (int m = 0; m < sh.nsm; ++m) {
-        kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'T'; kd.U[m] = factors[m + 2];
-      }
-      MES_TRY(mes::kron_build(kd, d.Kmat, done, st));
-      Fibres fb;
-      fb.F_lo = r1; fb.F_hi = r2;
-      fb.in = Bt; fb.in_lo = 1; fb.in_hi = r1 * L; fb.in_l = r1;
-      fb.out = core; fb.out_lo = 1; fb.out_hi = r1; fb.out_l = r1 * r2;
-      MES_TRY(mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, done, st));
+      MES_TRY(core_from_B(done));
       MES_TRY(mes::sumsq(core, r1 * r2 * Lr, qpart, nblk, done, st));
       MES_TRY(mes::sum_doubles(qpart, nblk, normQ, done, st));
       MES_TRY(mes::fit_flag(normX, normQ, sweep, tol, o.fit_history, fitlast, done, o.iters_done, st));
     }
   }
   d.skip = nullptr;
+
+  // ---- full-rank small modes: eigenvectors from the last sweep's B ----
+  {
+    bool any_full = false;
+    for (int n = 2; n < N; ++n)
+      if (sh.r[n] == sh.s[n]) {
+        MES_TRY(small_mode_update(n));
+        any_full = true;
+      }
+    if (any_full) MES_TRY(core_from_B(nullptr));
+  }
 
   // ---- canonical basis of the large modes ----
   if (canonical) {
@@ -632,8 +662,8 @@ extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims,
         gzz.B = d.cwX; gzz.b_n = r; gzz.b_k = 1;
         gzz.C = d.H; gzz.c_m = 1; gzz.c_n = r;
         MES_TRY(d.gemm(gzz));
-        MES_TRY(mes::chol(d.H, (int)r, 0.f, d.cwA, d.dinv, flags, nullptr, st));
-        MES_TRY(mes::trsm(d.cwX, r, (int)r, d.cwA, d.dinv, d.Rinv, false, nullptr, st));   // Z in Rinv
+        MES_TRY(mes::chol(d.H, (int)r, 0.f, d.cwA, d.dinv, d.linv, flags, nullptr, st));
+        MES_TRY(mes::trsm(d.cwX, r, (int)r, d.cwA, d.dinv, d.linv, d.Rinv, false, nullptr, st));   // Z in Rinv
         Gemm gu = base();  // W = S Z
         gu.M = s; gu.N = r; gu.K_lo = r;
         gu.A = S; gu.a_m = 1; gu.a_k = s;
@@ -716,4 +746,19 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
   MES_TRY(scr.alloc(&T2, sh.r1 * sh.s2 * sh.L));
   MES_TRY(scr.alloc(&Kmat, 16384));
   return mes_reconstruct_impl(sh, core, factors, out, ref, sse, scr, T1, T2, Kmat, st);
+}
+
+extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
+                                     int max_iters, double tol, float* core, float* const* factors,
+                                     double* fit, const mes_als_opts* opts, void* stream) {
+  mes::clear_error();
+  return tucker_als_impl(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, stream, nullptr);
+}
+
+extern "C" mes_status mes_tucker_als_workspace_size(int N, const int64_t* dims, const int64_t* ranks,
+                                                    const mes_als_opts* opts, size_t* bytes) {
+  mes::clear_error();
+  if (!bytes) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als_workspace_size: null pointer");
+  *bytes = 0;
+  return tucker_als_impl(nullptr, N, dims, ranks, 1, 0.0, nullptr, nullptr, nullptr, opts, nullptr, bytes);
 }

@@ -190,6 +190,23 @@ def test_ragged_shape_truncated_small_modes(mes):
             assert sin_max < 1e-3, (n, gap, sin_max)
 
 
+def test_mid_ranks_not_multiple_of_32(mes):
+    # ranks 150 and 140 (> 128, not multiples of the 32-column blocks of the
+    # cluster Cholesky and the blocked triangular solve) on a 400 x 300 scene
+    spec = synth.SceneSpec(400, 300, (0.5, 2.0), views=2, d_max=8)
+    img = synth.make_stack(spec, 77)
+    T = colour.colour_convert(img, "ipt")           # 400 x 300 x 3 x 4
+    ranks = (150, 140, 3, 4)
+    ref = tucker.hooi(T, ranks, 12, 0.0)
+    for prec in ("fp32", "tf32"):
+        res = _run(mes, T, ranks, 12, 0.0, precision=prec)
+        fit = float(res["fit"].cpu())
+        tol = 1e-5 if prec == "fp32" else 1e-4
+        assert abs(fit - ref.fit) / ref.fit < tol, (prec, fit, ref.fit)
+        for n, U in enumerate(factors_np(res)):
+            assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 2e-6, (prec, n)
+
+
 def test_full_multilinear_rank_is_exact(mes):
     rng = np.random.default_rng(5)
     T = rng.standard_normal((40, 24, 3, 4))
