@@ -30,6 +30,7 @@
 #ifndef MES_H
 #define MES_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -137,6 +138,22 @@ mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int6
                           double* fit, const mes_als_opts* opts, void* stream);
 
 /*
+ * mes_tucker_als_workspace_size -- device workspace that mes_tucker_als takes
+ * from the stream-ordered allocator for this shape and these options (each
+ * request rounded up to 256 bytes), without touching the device.  A caller
+ * that budgets device memory (the serving loop) admits a decomposition by
+ * this figure plus its own input and output buffers.  The paper has no
+ * counterpart; it is bookkeeping for the Section III-B decomposition.
+ *
+ *  N, dims, ranks, opts   as for mes_tucker_als.
+ *  bytes    [out] HOST size_t.
+ * Errors: as mes_tucker_als for the shape and options; MES_ERR_INVALID_ARG
+ *         for a null `bytes`.
+ */
+mes_status mes_tucker_als_workspace_size(int N, const int64_t* dims, const int64_t* ranks,
+                                         const mes_als_opts* opts, size_t* bytes);
+
+/*
  * mes_reconstruct -- T_hat = Q x_1 S^(1) x_2 ... x_N S^(N) (Eq. 1, Eq. 2).
  *
  *  core     [in]  FP32 tensor of dims `ranks`.
@@ -206,6 +223,111 @@ mes_status mes_quantize_core(const float* core, int N, const int64_t* ranks, int
  */
 mes_status mes_quantize_core_noalloc(const float* core, int N, const int64_t* ranks, int bits,
                                      int16_t* q, float* scales, void* stream);
+
+/*
+ * mes_problem -- one stack of the batched and served forms: the colour
+ * pre-pass (when rgb8 is given), the decomposition and the quantiser (when
+ * quant_bits > 0), exactly as mes_colour_convert, mes_tucker_als and
+ * mes_quantize_core would run them one after another on one stream, so each
+ * result is the same as that of the single calls.  Pointers are caller-owned
+ * DEVICE memory; dims, ranks and the factor pointers are held by value, so a
+ * problem may be a temporary.
+ */
+typedef struct mes_problem {
+  const uint8_t* rgb8;   /* nullable: K images laid out as for mes_colour_convert;
+                            then N = 4 and dims = (s1, s2, 3, K)            */
+  int space;             /* mes_colour of rgb8                              */
+  float gamma;           /* IPT linearisation exponent (0 means 2.2)        */
+  float* X;              /* FP32 tensor of dims: written when rgb8 is given,
+                            otherwise the input                             */
+  int N;                 /* order, 2..8                                     */
+  int64_t dims[8];
+  int64_t ranks[8];
+  int max_iters;
+  double tol;
+  mes_als_opts opts;     /* as for mes_tucker_als; all zero = defaults      */
+  float* core;
+  float* factors[8];
+  double* fit;           /* nullable device double                          */
+  int quant_bits;        /* 0 = no quantiser, else 2..16                    */
+  int16_t* q;            /* quantised core when quant_bits > 0              */
+  float* scales;         /* per-plane scales when quant_bits > 0            */
+} mes_problem;
+
+/*
+ * Batched form: many stacks of uneven size, rank and colour space in one
+ * submission.  The paper decomposes one stack at a time; this is the
+ * engineering form of Section III-B for many stacks.
+ *
+ * mes_batch_create(max_streams, out): a batch context on the current device
+ *   with max_streams (1..64) internal streams.  *out is a HOST handle.
+ * mes_batch_run(b, probs, n, statuses, stream): validates every problem
+ *   (statuses: nullable HOST array of n entries receiving each problem's
+ *   validation status; nothing is enqueued if any fails), orders them by
+ *   estimated work, longest first, and deals them to the internal streams so
+ *   each stream's total work is balanced; the streams are forked from and
+ *   joined back into `stream`, so all work is ordered after what `stream`
+ *   already holds and before what it gets next.
+ * mes_batch_capture(b, probs, n, stream): the same enqueue captured into one
+ *   CUDA graph held by the context (replacing any previous one); nothing
+ *   runs.  Call mes_batch_run once first on the same shapes so one-time setup
+ *   happens outside the capture.  The graph holds the problems' pointers.
+ * mes_batch_launch(b, stream): replays the captured graph on `stream`.
+ * mes_batch_destroy(b): frees the context (after its work completes).
+ * Errors: MES_ERR_INVALID_ARG (null handle or arrays, n < 1, a problem that
+ *   fails validation, launch without capture, capture while the kernel
+ *   profiler is on), errors of the single calls, MES_ERR_CUDA.
+ */
+typedef struct mes_batch mes_batch;
+mes_status mes_batch_create(int max_streams, mes_batch** out);
+mes_status mes_batch_run(mes_batch* b, const mes_problem* probs, int n, mes_status* statuses, void* stream);
+mes_status mes_batch_capture(mes_batch* b, const mes_problem* probs, int n, void* stream);
+mes_status mes_batch_launch(mes_batch* b, void* stream);
+mes_status mes_batch_destroy(mes_batch* b);
+
+/*
+ * Serving form: a request loop with continuous batching.  Requests are
+ * admitted in arrival order as soon as one of `max_slots` slots (each an
+ * internal stream) is free and the device memory they need fits in
+ * `hbm_budget_bytes` next to the requests already running; a request that
+ * does not fit lets later ones that do fit pass it (never more than
+ * max_slots of them).  A request's device memory is its workspace
+ * (mes_tucker_als_workspace_size plus the quantiser's planes) and its input
+ * and output buffers.  State stays on the device; the caller reads results
+ * from its own buffers after completion.  The paper has no counterpart; this
+ * serves Section III-B decompositions.
+ *
+ * mes_serve_create(hbm_budget_bytes, max_slots, out): starts the loop (one
+ *   host thread) on the current device.
+ * mes_serve_submit(s, p, ticket): validates and queues a copy of *p; HOST
+ *   *ticket receives its id.  MES_ERR_OOM if it can never fit the budget.
+ * mes_serve_poll(s, ticket, done, result, latency_ms): HOST outputs; *done 1
+ *   once the request's device work has completed, with its status and its
+ *   latency from submission to observed completion (nullable outputs).
+ * mes_serve_wait(s, ticket, timeout_ms, result, latency_ms): blocks until
+ *   done or timeout_ms (< 0: no limit); MES_ERR_TIMEOUT on timeout.
+ * mes_serve_get_stats(s, out): counts, latency percentiles of completed
+ *   requests and memory in use (HOST struct).
+ * mes_serve_destroy(s): waits for queued and running requests, stops the
+ *   loop and frees the server.
+ * Errors: MES_ERR_INVALID_ARG (null handle or pointer, unknown ticket,
+ *   budget 0, max_slots outside 1..64), MES_ERR_OOM, MES_ERR_TIMEOUT,
+ *   MES_ERR_CUDA.
+ */
+typedef struct mes_server mes_server;
+typedef struct mes_serve_stats {
+  uint64_t submitted, completed, failed, queued, running;
+  double p50_ms, p99_ms, max_ms, mean_ms;  /* submit-to-completion latency */
+  double first_admit_s, last_done_s;       /* host clock, seconds since creation */
+  size_t hbm_in_use, hbm_peak;
+} mes_serve_stats;
+mes_status mes_serve_create(size_t hbm_budget_bytes, int max_slots, mes_server** out);
+mes_status mes_serve_submit(mes_server* s, const mes_problem* p, uint64_t* ticket);
+mes_status mes_serve_poll(mes_server* s, uint64_t ticket, int* done, mes_status* result, double* latency_ms);
+mes_status mes_serve_wait(mes_server* s, uint64_t ticket, double timeout_ms, mes_status* result,
+                          double* latency_ms);
+mes_status mes_serve_get_stats(mes_server* s, mes_serve_stats* out);
+mes_status mes_serve_destroy(mes_server* s);
 
 /* Inverse of mes_quantize_core: x = q * scale (FP32), same layouts. */
 mes_status mes_dequantize_core(const int16_t* q, const float* scales, int N,

@@ -135,6 +135,20 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     return out
 
 
+def tucker_als_workspace_size(dims: Sequence[int], ranks: Sequence[int], precision: str = "fp32") -> int:
+    """Bytes of device workspace mes_tucker_als takes for this shape (no
+    device access)."""
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    opts = _lib.MesAlsOpts()
+    opts.precision = PRECISIONS[precision]
+    n = ctypes.c_size_t(0)
+    lib = _lib.load()
+    _lib.check(lib.mes_tucker_als_workspace_size(len(dims), _i64(dims), _i64(ranks), ctypes.byref(opts),
+                                                 ctypes.byref(n)), "mes_tucker_als_workspace_size")
+    return int(n.value)
+
+
 def reconstruct(core, factors, dims: Sequence[int], ranks: Sequence[int], out=None, ref=None):
     """T_hat = Q x_1 S^(1) ... x_N S^(N) (Eq. 1).  With `ref`, also returns
     sum((ref - T_hat)^2) as a float64 CUDA scalar (fused)."""
@@ -176,3 +190,160 @@ def dequantize_core(q, scales, ranks: Sequence[int]):
     st = lib.mes_dequantize_core(_ptr(q), _ptr(scales), len(ranks), _i64(ranks), _ptr(core), _stream())
     _lib.check(st, "mes_dequantize_core")
     return core
+
+
+class Problem:
+    """One stack for the batched and served forms: device buffers for the
+    input (8-bit images or the FP32 tensor) and every output, and the
+    `mes_problem` descriptor pointing at them.  Keep the object alive until
+    its work has completed."""
+
+    def __init__(self, dims: Sequence[int], ranks: Sequence[int], X=None, rgb8=None, space: str = "ipt",
+                 gamma: float = 2.2, max_iters: int = 20, tol: float = 0.0, precision: str = "fp32",
+                 quant_bits: int = 0, device=None):
+        torch = _torch()
+        dims = [int(d) for d in dims]
+        ranks = [int(r) for r in ranks]
+        N = len(dims)
+        if len(ranks) != N or not 2 <= N <= 8:
+            raise ValueError("dims and ranks must have the same length, 2..8")
+        src = rgb8 if rgb8 is not None else X
+        dev = device if device is not None else (src.device if src is not None else torch.device("cuda"))
+        if rgb8 is not None:
+            _need(rgb8, torch.uint8, "rgb8")
+            if N != 4 or dims[2] != 3 or tuple(rgb8.shape) != (dims[3], dims[1], dims[0], 3):
+                raise ValueError("rgb8 must be (K, s2, s1, 3) for dims (s1, s2, 3, K)")
+            X = torch.empty(torch_shape(dims), dtype=torch.float32, device=dev) if X is None else X
+        if X is None:
+            raise ValueError("give X or rgb8")
+        _need(X, torch.float32, "X")
+        self.dims, self.ranks, self.rgb8, self.X = dims, ranks, rgb8, X
+        self.core = torch.empty(torch_shape(ranks), dtype=torch.float32, device=dev)
+        self.factors = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
+        self.fit = torch.empty((), dtype=torch.float64, device=dev)
+        self.iters = torch.zeros((), dtype=torch.int32, device=dev)
+        P = 1
+        for r in ranks[2:]:
+            P *= r
+        self.q = torch.empty(torch_shape(ranks), dtype=torch.int16, device=dev) if quant_bits else None
+        self.scales = torch.empty((P,), dtype=torch.float32, device=dev) if quant_bits else None
+        p = _lib.MesProblem()
+        p.rgb8 = _ptr(rgb8)
+        p.space = SPACES[space]
+        p.gamma = float(gamma)
+        p.X = _ptr(X)
+        p.N = N
+        for n in range(N):
+            p.dims[n] = dims[n]
+            p.ranks[n] = ranks[n]
+            p.factors[n] = self.factors[n].data_ptr()
+        p.max_iters = int(max_iters)
+        p.tol = float(tol)
+        p.opts.precision = PRECISIONS[precision]
+        p.opts.iters_done = self.iters.data_ptr()
+        p.core = _ptr(self.core)
+        p.fit = _ptr(self.fit)
+        p.quant_bits = int(quant_bits)
+        p.q = _ptr(self.q)
+        p.scales = _ptr(self.scales)
+        self.struct = p
+
+
+def _problem_array(problems):
+    arr = (_lib.MesProblem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = p.struct
+    return arr
+
+
+class Batch:
+    """Batched form: `run` deals the problems to `max_streams` internal streams
+    (longest first, balanced), forked from and joined back into the current
+    stream; `capture` records the same enqueue as one CUDA graph that
+    `launch` replays."""
+
+    def __init__(self, max_streams: int = 8):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.mes_batch_create(int(max_streams), ctypes.byref(self._h)), "mes_batch_create")
+        self._keep = None
+
+    def run(self, problems):
+        arr = _problem_array(problems)
+        sts = (ctypes.c_int * len(problems))()
+        _lib.check(self._lib.mes_batch_run(self._h, arr, len(problems), sts, _stream()), "mes_batch_run")
+
+    def capture(self, problems, stream=None):
+        torch = _torch()
+        arr = _problem_array(problems)
+        self._keep = (arr, list(problems))
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(self._lib.mes_batch_capture(self._h, arr, len(problems), ctypes.c_void_p(st.cuda_stream)),
+                   "mes_batch_capture")
+
+    def launch(self):
+        _lib.check(self._lib.mes_batch_launch(self._h, _stream()), "mes_batch_launch")
+
+    def close(self):
+        if self._h:
+            self._lib.mes_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving form: a request loop admitting problems into `max_slots` slots
+    under a device-memory budget (continuous batching).  `submit` returns a
+    ticket; `wait`/`poll` give (status, latency in ms)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 8):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.mes_serve_create(ctypes.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                              ctypes.byref(self._h)), "mes_serve_create")
+        self._live = {}
+
+    def submit(self, problem: Problem) -> int:
+        t = ctypes.c_uint64()
+        _lib.check(self._lib.mes_serve_submit(self._h, ctypes.byref(problem.struct), ctypes.byref(t)),
+                   "mes_serve_submit")
+        self._live[t.value] = problem
+        return t.value
+
+    def poll(self, ticket: int):
+        done, res, lat = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _lib.check(self._lib.mes_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(res),
+                                            ctypes.byref(lat)), "mes_serve_poll")
+        if not done.value:
+            return None
+        self._live.pop(ticket, None)
+        return res.value, lat.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        res, lat = ctypes.c_int(), ctypes.c_double()
+        _lib.check(self._lib.mes_serve_wait(self._h, ctypes.c_uint64(ticket), float(timeout_ms), ctypes.byref(res),
+                                            ctypes.byref(lat)), "mes_serve_wait")
+        self._live.pop(ticket, None)
+        return res.value, lat.value
+
+    def stats(self) -> dict:
+        s = _lib.MesServeStats()
+        _lib.check(self._lib.mes_serve_get_stats(self._h, ctypes.byref(s)), "mes_serve_get_stats")
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.mes_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

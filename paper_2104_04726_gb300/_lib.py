@@ -33,11 +33,24 @@ SIGNATURES = {
                                       _p, _p, _p]),
     "mes_tucker_als": (_c.c_int, [_p, _c.c_int, _i64p, _i64p, _c.c_int, _c.c_double, _p,
                                   _c.POINTER(_p), _p, _p, _p]),
+    "mes_tucker_als_workspace_size": (_c.c_int, [_c.c_int, _i64p, _i64p, _p, _c.POINTER(_c.c_size_t)]),
     "mes_reconstruct": (_c.c_int, [_p, _c.POINTER(_p), _c.c_int, _i64p, _i64p, _p, _p, _p, _p]),
     "mes_quantize_core": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _c.c_int, _p]),
     "mes_dequantize_core": (_c.c_int, [_p, _p, _c.c_int, _i64p, _p, _p]),
     "mes_quantize_core_noalloc": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _p]),
     "mes_gemm_selftest": (_c.c_int, [_c.c_int, _p, _p, _p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _p]),
+    "mes_batch_create": (_c.c_int, [_c.c_int, _c.POINTER(_p)]),
+    "mes_batch_run": (_c.c_int, [_p, _p, _c.c_int, _c.POINTER(_c.c_int), _p]),
+    "mes_batch_capture": (_c.c_int, [_p, _p, _c.c_int, _p]),
+    "mes_batch_launch": (_c.c_int, [_p, _p]),
+    "mes_batch_destroy": (_c.c_int, [_p]),
+    "mes_serve_create": (_c.c_int, [_c.c_size_t, _c.c_int, _c.POINTER(_p)]),
+    "mes_serve_submit": (_c.c_int, [_p, _p, _c.POINTER(_c.c_uint64)]),
+    "mes_serve_poll": (_c.c_int, [_p, _c.c_uint64, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
+                                  _c.POINTER(_c.c_double)]),
+    "mes_serve_wait": (_c.c_int, [_p, _c.c_uint64, _c.c_double, _c.POINTER(_c.c_int), _c.POINTER(_c.c_double)]),
+    "mes_serve_get_stats": (_c.c_int, [_p, _p]),
+    "mes_serve_destroy": (_c.c_int, [_p]),
     "mes_profile_enable": (None, [_c.c_int]),
     "mes_profile_count": (_c.c_int, []),
     "mes_profile_get": (_c.c_int, [_c.c_int, _c.c_char_p, _c.c_int, _i64p, _c.POINTER(_c.c_double),
@@ -56,6 +69,47 @@ class MesAlsOpts(ctypes.Structure):
         ("iters_done", ctypes.c_void_p),
         ("fit_history", ctypes.c_void_p),
         ("canonical", ctypes.c_int),
+    ]
+
+
+class MesProblem(ctypes.Structure):
+    """Mirror of `mes_problem` in include/mes.h."""
+    _fields_ = [
+        ("rgb8", ctypes.c_void_p),
+        ("space", ctypes.c_int),
+        ("gamma", ctypes.c_float),
+        ("X", ctypes.c_void_p),
+        ("N", ctypes.c_int),
+        ("dims", ctypes.c_int64 * 8),
+        ("ranks", ctypes.c_int64 * 8),
+        ("max_iters", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("opts", MesAlsOpts),
+        ("core", ctypes.c_void_p),
+        ("factors", ctypes.c_void_p * 8),
+        ("fit", ctypes.c_void_p),
+        ("quant_bits", ctypes.c_int),
+        ("q", ctypes.c_void_p),
+        ("scales", ctypes.c_void_p),
+    ]
+
+
+class MesServeStats(ctypes.Structure):
+    """Mirror of `mes_serve_stats` in include/mes.h."""
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("failed", ctypes.c_uint64),
+        ("queued", ctypes.c_uint64),
+        ("running", ctypes.c_uint64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
+        ("first_admit_s", ctypes.c_double),
+        ("last_done_s", ctypes.c_double),
+        ("hbm_in_use", ctypes.c_size_t),
+        ("hbm_peak", ctypes.c_size_t),
     ]
 
 

@@ -83,17 +83,28 @@ struct Scratch {
   cudaStream_t stream;
   void* ptrs[64];
   int n = 0;
-  explicit Scratch(cudaStream_t s) : stream(s) {}
+  // dry: nothing is allocated; `total` sums the bytes a real run would take
+  // (each request rounded up to 256 bytes) and the returned pointers are
+  // placeholders that must not be used
+  bool dry = false;
+  size_t total = 0;
+  explicit Scratch(cudaStream_t s, bool dry_run = false) : stream(s), dry(dry_run) {}
   ~Scratch() {
     for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], stream);
   }
   template <class T>
   mes_status alloc(T** out, size_t count) {
-    if (n >= 64) return fail(MES_ERR_OOM, "scratch table full");
-    void* p = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~size_t(255), stream);
+    const size_t rounded = (bytes + 255) & ~size_t(255);
+    total += rounded;
+    if (dry) {
+      *out = reinterpret_cast<T*>(uintptr_t(256));
+      return MES_OK;
+    }
+    if (n >= 64) return fail(MES_ERR_OOM, "scratch table full");
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, rounded, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(MES_ERR_OOM, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));

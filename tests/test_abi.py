@@ -75,3 +75,59 @@ def test_validation_without_gpu(lib):
     assert lib.mes_quantize_core(fake, 2, _i64([4, 4]), 17, fake, fake, 0, None) == 1
     assert lib.mes_quantize_core(None, 2, _i64([4, 4]), 8, fake, fake, 0, None) == 1
     assert lib.mes_reconstruct(fake, facs, 4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), fake, fake, None, None) == 1
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a tiny C program."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    out_dir = os.path.join(ROOT, "paper_2104_04726_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, f"layout_{struct}.c")
+    exe = os.path.join(out_dir, f"layout_{struct}")
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    with open(src, "w") as fh:
+        fh.write('#include <stddef.h>\n#include <stdio.h>\n#include "mes.h"\nint main(void) {\n'
+                 f'  printf("%zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    vals = [int(x) for x in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("struct,cls", [("mes_als_opts", "MesAlsOpts"), ("mes_problem", "MesProblem"),
+                                        ("mes_serve_stats", "MesServeStats")])
+def test_struct_layout_matches_c(struct, cls):
+    from paper_2104_04726_gb300 import _lib
+    C = getattr(_lib, cls)
+    names = [f for f, _ in C._fields_]
+    size, offs = _c_layout(struct, names)
+    assert size == ctypes.sizeof(C)
+    assert offs == [getattr(C, f).offset for f in names]
+
+
+def test_batch_and_server_validation_without_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.mes_batch_create(0, ctypes.byref(h)) == 1
+    assert lib.mes_batch_create(65, ctypes.byref(h)) == 1
+    assert lib.mes_batch_run(None, None, 1, None, None) == 1
+    assert lib.mes_batch_launch(None, None) == 1
+    assert lib.mes_serve_create(0, 2, ctypes.byref(h)) == 1
+    assert lib.mes_serve_create(1 << 30, 0, ctypes.byref(h)) == 1
+    assert lib.mes_serve_submit(None, None, None) == 1
+    assert lib.mes_batch_destroy(None) == 0 and lib.mes_serve_destroy(None) == 0
+
+
+def test_workspace_size_query_without_gpu(lib):
+    import paper_2104_04726_gb300 as mes
+    a = mes.tucker_als_workspace_size([64, 48, 3, 6], [16, 12, 3, 6])
+    b = mes.tucker_als_workspace_size([128, 96, 3, 6], [16, 12, 3, 6])
+    c = mes.tucker_als_workspace_size([64, 48, 3, 6], [16, 12, 3, 6], "tf32")
+    assert 0 < a < b
+    # the TF32 form keeps a rounded copy of T and of the two large factors
+    assert c - a >= 64 * 48 * 18 * 4
+    n = ctypes.c_size_t()
+    assert lib.mes_tucker_als_workspace_size(4, _i64([8, 6, 3, 2]), _i64([9, 2, 1, 1]), None, ctypes.byref(n)) == 2
+    assert lib.mes_tucker_als_workspace_size(4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), None, None) == 1
