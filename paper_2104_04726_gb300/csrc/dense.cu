@@ -40,10 +40,14 @@ constexpr int kChol = 256;
 
 // One column step of the 32 x 32 factorization held one row per lane in
 // registers; J is a compile-time index so row[] never spills to local memory.
+// The pivot of step J+1 is formed and broadcast before the column update so
+// the serial chain per step is shuffle -> rsqrt -> multiply -> FMA; the
+// scaled column J goes through shared memory (colbuf row J) and is read back
+// as float4 broadcasts.  rdiag[J] receives 1 / L_JJ.
 template <int J>
-__device__ __forceinline__ void chol_step(float (&row)[PB], int lane, int b, float floor, int* bad) {
+__device__ __forceinline__ void chol_step(float (&row)[PB], float piv, int lane, int b, float floor, int* bad,
+                                          float* colbuf, float* rdiag) {
   if constexpr (J < PB) {
-    float piv = __shfl_sync(0xffffffffu, row[J], J);
     if (J < b) {
       if (!(piv > floor)) {
         if (lane == 0) *bad = 1;
@@ -53,15 +57,29 @@ __device__ __forceinline__ void chol_step(float (&row)[PB], int lane, int b, flo
       piv = 1.f;
     }
     const float rs = rsqrtf(piv);
-    if (lane == J) row[J] = piv * rs;
-    else if (lane > J) row[J] *= rs;
-    const float lij = row[J];
+    const float l = (lane == J) ? piv * rs : row[J] * rs;
+    if (lane >= J) row[J] = l;
+    if (lane == J) rdiag[J] = rs;
+    if constexpr (J + 1 < PB) {
+      // the next pivot first: lane J+1 holds it and needs only its own l
+      // (the same value the column update below gives it)
+      const float next = __shfl_sync(0xffffffffu, fmaf(-l, l, row[J + 1]), J + 1);
+      colbuf[J * PB + lane] = (lane > J) ? l : 0.f;
+      __syncwarp();
+      constexpr int K0 = (J + 1) & ~3;
 #pragma unroll
-    for (int k = J + 1; k < PB; ++k) {
-      const float lkj = __shfl_sync(0xffffffffu, row[J], k);
-      if (lane >= k) row[k] = fmaf(-lij, lkj, row[k]);
+      for (int k4 = K0; k4 < PB; k4 += 4) {
+        const float4 c = *reinterpret_cast<const float4*>(colbuf + J * PB + k4);
+        const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          // lanes < k only touch the upper part, which is never read
+          const int k = k4 + u;
+          if (k > J) row[k] = fmaf(-l, cv[u], row[k]);
+        }
+      }
+      chol_step<J + 1>(row, next, lane, b, floor, bad, colbuf, rdiag);
     }
-    chol_step<J + 1>(row, lane, b, floor, bad);
   }
 }
 
@@ -84,12 +102,37 @@ __device__ __forceinline__ void warp_tri_inv32(const float* Ls, float* __restric
   for (int i = 0; i < PB; ++i) out[i * PB + lane] = x[i];
 }
 
-__device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad) {
+// One column of the forward substitution x L^T = a for a row held in
+// registers: colbuf row C holds column C of L below the diagonal, rdiag the
+// reciprocals of its diagonal.  C is a compile-time index (no local memory).
+template <int C>
+__device__ __forceinline__ void panel_step(float (&a)[PB], const float* colbuf, const float* rdiag) {
+  if constexpr (C < PB) {
+    const float x = a[C] * rdiag[C];
+    a[C] = x;
+#pragma unroll
+    for (int j4 = (C + 1) & ~3; j4 < PB; j4 += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(colbuf + C * PB + j4);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j4 + u > C) a[j4 + u] = fmaf(-x, vv[u], a[j4 + u]);
+    }
+    asm volatile("" ::: "memory");   // keep the next column's loads after this one's
+    panel_step<C + 1>(a, colbuf, rdiag);
+  }
+}
+
+// 32 x 32 diagonal block (rows of Dg with stride 33, lower part; rows/cols
+// at and beyond b are treated as identity) -> L in place (upper part zeroed)
+// and rdiag = 1 / diag(L).  colbuf: 32 x 32 floats of shared memory, 16-byte
+// aligned.  One warp.
+__device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* bad, float* colbuf, float* rdiag) {
   const int lane = threadIdx.x & 31;
   float row[PB];
 #pragma unroll
   for (int k = 0; k < PB; ++k) row[k] = (k <= lane && lane < b && k < b) ? Dg[lane * (PB + 1) + k] : (k == lane ? 1.f : 0.f);
-  chol_step<0>(row, lane, b, floor, bad);
+  chol_step<0>(row, __shfl_sync(0xffffffffu, row[0], 0), lane, b, floor, bad, colbuf, rdiag);
 #pragma unroll
   for (int k = 0; k < PB; ++k) Dg[lane * (PB + 1) + k] = (k <= lane) ? row[k] : 0.f;
 }
@@ -104,6 +147,7 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
   float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
   __shared__ int bad;
   __shared__ float Drc[PB];                 // reciprocals of the diagonal of L_pp
+  __shared__ __align__(16) float colbuf[PB * PB];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   // flags[0]: error bits; flags[1]: calls; flags[2]: shift restarts
   if (t == 0 && flags) atomicAdd(flags + 1, 1);
@@ -140,11 +184,7 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
         Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? A[(p0 + i) + (int64_t)r * (p0 + j)] : 0.f;
       }
       __syncthreads();
-      if (warp == 0) {
-        warp_chol32(Dg, b, floor, &bad);
-        __syncwarp();
-        Drc[lane] = 1.f / Dg[lane * (PB + 1) + lane];
-      }
+      if (warp == 0) warp_chol32(Dg, b, floor, &bad, colbuf, Drc);
       __syncthreads();
       for (int e = t; e < b * b; e += kChol) {
         int i = e % b, j = e / b;
@@ -249,6 +289,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
   float* Pn = Dg + PB * (PB + 1);           // up to 1024 x 33 (panel)
   __shared__ int bad;
   __shared__ float Drc[PB];                 // reciprocals of the diagonal of L_pp
+  __shared__ __align__(16) float colbuf[PB * PB];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   if (rank == 0 && t == 0 && flags) atomicAdd(flags + 1, 1);
 
@@ -284,11 +325,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
         Dg[i * (PB + 1) + j] = (i < b && j < b && i >= j) ? __ldcg(A + (p0 + i) + (int64_t)r * (p0 + j)) : 0.f;
       }
       __syncthreads();
-      if (warp == 0) {
-        warp_chol32(Dg, b, floor, &bad);
-        __syncwarp();
-        Drc[lane] = 1.f / Dg[lane * (PB + 1) + lane];
-      }
+      if (warp == 0) warp_chol32(Dg, b, floor, &bad, colbuf, Drc);
       __syncthreads();
       if (rank == 0)
         for (int e = t; e < b * b; e += kChol) {
@@ -393,6 +430,7 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 // CTA reads it after the same barrier, so all restart together.
 // --------------------------------------------------------------------------
 constexpr int kDsmMaxR = 512;
+static_assert(kChol == 256, "the diagonal-block update maps 8 warps to 32 columns");
 constexpr int LD = PB + 1;
 
 __device__ __forceinline__ int dsm_slot_offset(int rank, int slot, int rp) {
@@ -405,10 +443,10 @@ __host__ __device__ inline size_t chol_dsm_smem(int r) {
   const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
   int rows = 0;  // CTA 0 holds the most rows
   for (int k = 0; k < nb; k += kCL) rows += rp - PB * k;
-  return (size_t)((rows + rp) * LD + rp) * sizeof(float);
+  return (size_t)((rows + rp) * LD + rp + 8) * sizeof(float);
 }
 
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol)
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol, 1)
 chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
                 float* __restrict__ dinv_out, float* __restrict__ Linv_blk, int* __restrict__ flags,
                 const int* __restrict__ skip) {
@@ -417,12 +455,13 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
   const int rank = (int)cluster.block_rank();
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   float* dinv = smem;              // rp
   float* store = dinv + rp;        // owned block columns
   int store_rows = 0;
   for (int k = rank; k < nb; k += kCL) store_rows += rp - PB * k;
-  float* Pl = store + store_rows * LD;  // copied panel rows
+  // panel rows read from L (row stride 33)
+  float* Pl_alloc = smem + rp + store_rows * LD;
   // bad-pivot flags per attempt and step parity; CTA 0's copy is the
   // cluster's.  A factor in step p reports to [p & 1]; the flag is read at the
   // top of step p + 1, before anyone can reach step p + 2 and write that
@@ -430,6 +469,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
   __shared__ int badv[8][2];
   __shared__ int lbad;
   __shared__ float Drc[PB];
+  __shared__ __align__(16) float colbuf[PB * PB];
   if (t < 16) badv[t >> 1][t & 1] = 0;
   if (rank == 0 && t == 0 && flags) atomicAdd(flags + 1, 1);
   for (int i = t; i < rp; i += kChol) {
@@ -446,40 +486,39 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
   volatile int* bad0 = cluster.map_shared_rank(&badv[0][0], 0);
   cluster.sync();  // every badv zeroed before anyone can report
 
-  // the owner factors its column k: 32 x 32 diagonal block in registers by
-  // warp 0, then the rows below by forward substitution (one row a thread)
-  auto factor_col = [&](float* Sk, int k, float floor) {
-    const int b = min(PB, r - PB * k);
-    if (warp == 0) {
-      warp_chol32(Sk, b, floor, &lbad);
-      __syncwarp();
-      Drc[lane] = 1.f / Sk[lane * LD + lane];
-    }
-    __syncthreads();
+  // rows 32 .. h-1 of the owner's column k solve x L_kk^T = a (one row a
+  // thread); colbuf row c holds column c of L_kk below the diagonal and is
+  // read as float4 broadcasts
+  auto panel_solve = [&](float* Sk, int k) {
     const int h = rp - PB * k;
     for (int i = PB + t; i < h; i += kChol) {
       float a[PB];
 #pragma unroll
       for (int c = 0; c < PB; ++c) a[c] = Sk[i * LD + c];
-#pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        const float x = a[c] * Drc[c];
-        a[c] = x;
-#pragma unroll
-        for (int j = c + 1; j < PB; ++j) a[j] = fmaf(-x, Sk[j * LD + c], a[j]);
-      }
+      panel_step<0>(a, colbuf, Drc);
 #pragma unroll
       for (int c = 0; c < PB; ++c) Sk[i * LD + c] = a[c];
     }
   };
-  // apply the copied panel (rows g_lo .. rp-1 in Pl) to owned column k:
-  // warp items of 128 rows x 4 columns, lane = row (+32 x), 4 x 4 registers
-  auto update_col = [&](float* Sk, int k, int g_lo) {
-    const int h = rp - PB * k;
-    const int items = ((h + 127) / 128) * 8;
-    const float* prow = Pl + (PB * k - g_lo) * LD;
-    for (int it = warp; it < items; it += kChol / 32) {
-      const int i0 = (it >> 3) * 128 + lane, c0 = (it & 7) * 4;
+  // the owner writes its factored column k (lower part) to L, where it is
+  // final and where the other CTAs read it as the next panel (through L2)
+  auto publish = [&](const float* Sk, int k) {
+    const int hr = r - PB * k;
+    const int w = min(PB, hr);
+    float* Lk = Lout + (PB * k) + (int64_t)r * (PB * k);
+    for (int i = t; i < hr; i += kChol)
+#pragma unroll 8
+      for (int c = 0; c < w; ++c)
+        if (i >= c) __stcg(Lk + i + (int64_t)r * c, Sk[i * LD + c]);
+  };
+  // apply the copied panel (global rows g_lo .. rp-1 at P) to rows
+  // [i_begin, i_end) of owned column k, by warps w0 .. w0+nw-1: items of 128
+  // rows x 4 columns, lane = row (+32 x), 4 x 4 registers
+  auto update_col = [&](float* Sk, int k, const float* P, int g_lo, int i_begin, int i_end, int w0, int nw) {
+    const int items = ((i_end - i_begin + 127) / 128) * 8;
+    const float* prow = P + (PB * k - g_lo) * LD;
+    for (int it = warp - w0; it < items; it += nw) {
+      const int i0 = i_begin + (it >> 3) * 128 + lane, c0 = (it & 7) * 4;
       const float* pc = prow + c0 * LD;
       float acc[4][4];
 #pragma unroll
@@ -490,7 +529,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
       for (int q = 0; q < PB; ++q) {
         float u[4], v[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) u[x] = (i0 + 32 * x < h) ? prow[(i0 + 32 * x) * LD + q] : 0.f;
+        for (int x = 0; x < 4; ++x) u[x] = (i0 + 32 * x < i_end) ? prow[(i0 + 32 * x) * LD + q] : 0.f;
 #pragma unroll
         for (int y = 0; y < 4; ++y) v[y] = pc[y * LD + q];
 #pragma unroll
@@ -501,7 +540,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         const int i = i0 + 32 * x;
-        if (i < h)
+        if (i < i_end)
 #pragma unroll
           for (int y = 0; y < 4; ++y) Sk[i * LD + c0 + y] -= acc[x][y];
       }
@@ -530,8 +569,11 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     }
     __syncthreads();
     if (rank == 0) {
-      factor_col(store, 0, floor);
+      if (warp == 0) warp_chol32(store, min(PB, r), floor, &lbad, colbuf, Drc);
       __syncthreads();
+      panel_solve(store, 0);
+      __syncthreads();
+      publish(store, 0);
       if (t == 0 && lbad) bad0[2 * attempt + 1] = 1;  // step -1
     }
     cluster.sync();
@@ -541,25 +583,63 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
       int kmin = rank;
       while (kmin <= p) kmin += kCL;
       if (kmin < nb) {
+        // panel p, rows g_lo .. rp-1: the owner uses its own copy, the
+        // others read it from L (column-major, written before the barrier)
         const int owner = p % kCL, g_lo = PB * kmin;
-        const float* src = cluster.map_shared_rank(store, owner) +
-                           (dsm_slot_offset(owner, p / kCL, rp) + (g_lo - PB * p)) * LD;
-        const int n = (rp - g_lo) * LD;
-        for (int e = t; e < n; e += kChol) Pl[e] = src[e];
+        const float* P;
+        if (owner == rank) {
+          P = store + (dsm_slot_offset(rank, p / kCL, rp) + (g_lo - PB * p)) * LD;
+        } else {
+          const int nrows = rp - g_lo;
+          const float* Lp = Lout + (int64_t)r * (PB * p) + g_lo;
+          for (int i = t; i < nrows; i += kChol) {
+            const bool in = g_lo + i < r;
+            float v[PB];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) v[c] = in ? __ldcg(Lp + i + (int64_t)r * c) : 0.f;
+#pragma unroll
+            for (int c = 0; c < PB; ++c) Pl_alloc[i * LD + c] = v[c];
+          }
+          P = Pl_alloc;
+        }
         __syncthreads();
         int slot = (kmin - rank) / kCL;
         int off = dsm_slot_offset(rank, slot, rp);
-        if (kmin == p + 1) {  // look-ahead: next panel first
+        if (kmin == p + 1) {
+          // look-ahead on the next column: its diagonal block is updated
+          // first and factored by warp 0 while warps 1..7 update the rows
+          // below; then every thread solves the panel
           float* Sk = store + off * LD;
-          update_col(Sk, kmin, g_lo);
+          const int h = rp - PB * kmin;
+          {
+            // diagonal block: thread t owns row t % 32, columns 4 (t / 32) + y
+            const float* prow = P + (PB * kmin - g_lo) * LD;
+            const int i = t & 31, c0 = (t >> 5) * 4;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+            for (int q = 0; q < PB; ++q) {
+              const float u = prow[i * LD + q];
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[y] = fmaf(u, prow[(c0 + y) * LD + q], acc[y]);
+            }
+#pragma unroll
+            for (int y = 0; y < 4; ++y) Sk[i * LD + c0 + y] -= acc[y];
+          }
           __syncthreads();
-          factor_col(Sk, kmin, floor);
+          if (warp == 0)
+            warp_chol32(Sk, min(PB, r - PB * kmin), floor, &lbad, colbuf, Drc);
+          else
+            update_col(Sk, kmin, P, g_lo, PB, h, 1, kChol / 32 - 1);
           __syncthreads();
+          panel_solve(Sk, kmin);
+          __syncthreads();
+          publish(Sk, kmin);
           if (t == 0 && lbad) bad0[2 * attempt + (p & 1)] = 1;
-          off += rp - PB * kmin;
+          off += h;
           kmin += kCL;
         }
-        for (int k = kmin; k < nb; off += rp - PB * k, k += kCL) update_col(store + off * LD, k, g_lo);
+        for (int k = kmin; k < nb; off += rp - PB * k, k += kCL)
+          update_col(store + off * LD, k, P, g_lo, 0, rp - PB * k, 0, kChol / 32);
       }
       cluster.sync();
     }
@@ -573,18 +653,10 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     if (rel > 1e-2f) rel = 1e-2f;
     cluster.sync();
   }
-  // L (lower triangle, column-major) and the inverses of the owned diagonal
-  // blocks (one warp each)
-  for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += kCL, ++q) {
-    const int h = rp - PB * k;
-    const float* Sk = store + off * LD;
-    if (warp == q) warp_tri_inv32(Sk, Linv_blk + (size_t)k * PB * PB);
-    for (int e = t; e < h * PB; e += kChol) {
-      const int i = e % h, c = e / h;
-      const int g = PB * k + i, j = PB * k + c;
-      if (g < r && j < r && g >= j) Lout[g + (int64_t)r * j] = Sk[i * LD + c];
-    }
-  }
+  // L is already in place (each column written when factored); the inverses
+  // of the owned diagonal blocks, one warp each
+  for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += kCL, ++q)
+    if (warp == q) warp_tri_inv32(store + off * LD, Linv_blk + (size_t)k * PB * PB);
 }
 
 // Inverses of the diagonal 32 x 32 blocks of L (global, column-major), one
