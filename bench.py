@@ -238,6 +238,103 @@ def _roofline(fams, peaks, peak_src, sms):
     return roof
 
 
+SERVE_SIZES = ((640, 480), (1280, 720), (1920, 1080))
+
+
+def measure_serving(mes, dev, precision, n_req, rate, seed, slots, budget_gb):
+    """Serving form: a Poisson request stream (`rate` per second, `n_req`
+    requests) of stacks drawn like the mixed workload -- 640x480, 1280x720 or
+    1920x1080 with 3..7 exposures per view, or 3840x2160 with 3 exposures at
+    5% -- ranks 20% of the two image modes (full rank for colour and
+    view x exposure), IPT or Y'CbCr at random, 20 sweeps, 16-bit quantised
+    core.  Requests are submitted at their arrival times to the library's
+    serving loop (continuous batching under a device-memory budget); latency
+    is submission to completion.  Beside it, one request of each size through
+    the plain FP32 path alone on one stream."""
+    import numpy as np
+    import torch
+    import synth
+
+    rng = np.random.default_rng(seed)
+    stops = tuple(2.0 ** e for e in (-3, -2, -1, 0, 1, 2, 3))
+    scenes = {}
+    for s1, s2 in SERVE_SIZES:
+        spec = synth.SceneSpec(s1, s2, stops, views=2, d_max=max(4, s1 // 40))
+        scenes[(s1, s2)] = torch.from_numpy(synth.make_stack(spec, 5000 + s1)).to(dev)
+    spec4k = synth.SceneSpec(3840, 2160, (0.25, 1.0, 4.0), views=2, d_max=96)
+    scenes[(3840, 2160)] = torch.from_numpy(synth.make_stack(spec4k, 5999)).to(dev)
+
+    def draw():
+        if rng.random() < 0.05:
+            s1, s2, E = 3840, 2160, 3
+        else:
+            s1, s2 = SERVE_SIZES[int(rng.integers(3))]
+            E = int(rng.integers(3, 8))
+        base = scenes[(s1, s2)]
+        Eb = base.shape[0] // 2
+        rgb = torch.cat([base[:E], base[Eb:Eb + E]]).contiguous()   # view-major, first E exposures
+        dims = (s1, s2, 3, 2 * E)
+        ranks = (round(0.2 * s1), round(0.2 * s2), 3, 2 * E)
+        space = "ipt" if rng.random() < 0.5 else "ycbcr"
+        return dims, ranks, rgb, space
+
+    def problem(d, prec):
+        dims, ranks, rgb, space = d
+        return mes.Problem(dims, ranks, rgb8=rgb, space=space, max_iters=20, tol=0.0, precision=prec,
+                           quant_bits=16)
+
+    reqs = [draw() for _ in range(n_req)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    probs = [problem(d, precision) for d in reqs]
+    # warm-up: one request of each size through the server (one-time setup)
+    srv = mes.Server(int(budget_gb * 2 ** 30), slots)
+    for d in {(r[0][0], r[0][1]): r for r in reqs}.values():
+        w = problem(d, precision)
+        srv.wait(srv.submit(w))
+    srv.close()
+    torch.cuda.synchronize()
+    srv = mes.Server(int(budget_gb * 2 ** 30), slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for a, p in zip(arrivals, probs):
+        dt = t0 + a - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(p))
+    lat, bad = [], 0
+    for t in tickets:
+        st, ms = srv.wait(t)
+        if st == 0:
+            lat.append(ms)
+        else:
+            bad += 1
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    eq = sum(d[0][0] * d[0][1] * d[0][3] for d in reqs) / (1920 * 1080 * 10)
+    fits = [float(p.fit) for p in probs]
+    # plain FP32 path, one request of each size alone on one stream
+    fp32 = {}
+    for d in {(r[0][0], r[0][1]): r for r in reqs}.values():
+        p = problem(d, "fp32")
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        b = mes.Batch(1)
+        b.run([p])
+        torch.cuda.synchronize()
+        fp32[f"{d[0][0]}x{d[0][1]}x3x{d[0][3]}"] = round(1e3 * (time.perf_counter() - a0), 2)
+        b.close()
+    lat_np = np.array(lat) if lat else np.array([float("nan")])
+    return {"requests": n_req, "rate_per_s": rate, "completed": len(lat), "failed": bad, "precision": precision,
+            "slots": slots, "hbm_budget_gib": budget_gb,
+            "p50_ms": float(np.percentile(lat_np, 50)), "p99_ms": float(np.percentile(lat_np, 99)),
+            "max_ms": float(lat_np.max()), "stacks_per_s": len(lat) / wall,
+            "fhd_equiv_stacks_per_s": eq / wall, "offered_fhd_equiv_per_s": eq / arrivals[-1],
+            "wall_s": wall, "hbm_peak_gib": stats["hbm_peak"] / 2 ** 30,
+            "all_fits_finite": bool(all(np.isfinite(fits))),
+            "fp32_alone_ms": fp32}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,6 +347,9 @@ def main():
                     help="skip timing the plain FP32 path beside the chosen precision form")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--stacks", type=int, default=8, help="independent stacks per step, one CUDA stream each")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving measurement (0 = skip it)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -420,6 +520,9 @@ def main():
             line["fp32_path"] = {"value": fp32["value"], "ms_per_step": fp32["ms_per_step"], "fit": fp32["fit"],
                                  "speedup": res["value"] / fp32["value"], "max_rel_fit_dev": dev_rel,
                                  "clocks": fp32["clocks"]}
+        if args.serve_requests > 0 and world == 1:
+            line["serve"] = measure_serving(mes, dev, args.precision, args.serve_requests, args.serve_rate,
+                                            seed=7, slots=8, budget_gb=96)
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

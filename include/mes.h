@@ -55,7 +55,12 @@ typedef enum mes_colour {
 
 typedef enum mes_precision {
   MES_PREC_FP32 = 0,  /* every contraction in FP32 (CUDA cores)            */
-  MES_PREC_BF16 = 1,  /* tensor-core BF16 inputs, FP32 accumulation        */
+  MES_PREC_BF16 = 1,  /* products with T as an operand (the mode products
+                         of Eq. 8 and of the T-HOSVD) on BF16 copies of T
+                         and the factors, FP32 accumulation; the factored
+                         Gram products as in MES_PREC_TF32; the returned
+                         core from T itself.  Needs s_1, s_2 multiples of
+                         8 (16-byte BF16 rows), else runs as MES_PREC_TF32 */
   MES_PREC_TF32 = 2   /* tensor-core TF32 inputs (FP32 data), FP32 accum.  */
 } mes_precision;
 

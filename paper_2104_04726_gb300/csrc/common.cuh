@@ -34,6 +34,20 @@ __host__ __device__ __forceinline__ float round_tf32(float x) {
 #endif
 }
 
+// Round to the nearest BF16 value (7 explicit mantissa bits), ties to even,
+// returned as its 16-bit pattern.  Inf and NaN keep their class.
+__host__ __device__ __forceinline__ uint16_t bf16_bits(float x) {
+#ifdef __CUDA_ARCH__
+  unsigned u = __float_as_uint(x);
+#else
+  unsigned u;
+  memcpy(&u, &x, 4);
+#endif
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
 // Records a formatted message in the thread-local error buffer and returns s.
 mes_status fail(mes_status s, const char* fmt, ...);
 void clear_error();

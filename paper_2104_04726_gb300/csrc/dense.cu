@@ -139,8 +139,13 @@ __device__ __forceinline__ void warp_chol32(float* Dg, int b, float floor, int* 
 
 __global__ void __launch_bounds__(kChol)
 chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ A,
-            float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+            float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip,
+            int* __restrict__ clean) {
+  if (skip && *skip) {
+    if (clean && threadIdx.x == 0) *clean = 1;
+    return;
+  }
+  int restarts = 0;
   extern __shared__ float smem[];
   float* dinv = smem;                       // 1024
   float* Dg = dinv + 1024;                  // 32 x 33
@@ -260,10 +265,12 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
       atomicOr(flags, 1);
       atomicAdd(flags + 2, 1);
     }
+    ++restarts;
     rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
     if (rel > 1e-2f) rel = 1e-2f;
     __syncthreads();
   }
+  if (clean && t == 0) *clean = restarts == 0;
 }
 
 // --------------------------------------------------------------------------
@@ -279,8 +286,13 @@ constexpr int kCL = 8;
 
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol)
 chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ A,
-                    float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip) {
-  if (skip && *skip) return;
+                    float* __restrict__ dinv_out, int* __restrict__ flags, const int* __restrict__ skip,
+                    int* __restrict__ clean) {
+  if (skip && *skip) {
+    if (clean && blockIdx.x == 0 && threadIdx.x == 0) *clean = 1;
+    return;
+  }
+  int restarts = 0;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ float smem[];
@@ -410,10 +422,12 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
       atomicOr(flags, 1);
       atomicAdd(flags + 2, 1);
     }
+    ++restarts;
     rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
     if (rel > 1e-2f) rel = 1e-2f;
     __syncthreads();
   }
+  if (clean && rank == 0 && t == 0) *clean = restarts == 0;
 }
 
 // --------------------------------------------------------------------------
@@ -449,8 +463,12 @@ __host__ __device__ inline size_t chol_dsm_smem(int r) {
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol, 1)
 chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
                 float* __restrict__ dinv_out, float* __restrict__ Linv_blk, int* __restrict__ flags,
-                const int* __restrict__ skip) {
-  if (skip && *skip) return;
+                const int* __restrict__ skip, int* __restrict__ clean) {
+  if (skip && *skip) {
+    if (clean && blockIdx.x == 0 && threadIdx.x == 0) *clean = 1;
+    return;
+  }
+  int restarts = 0;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -649,10 +667,12 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
       atomicOr(flags, 1);
       atomicAdd(flags + 2, 1);
     }
+    ++restarts;
     rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
     if (rel > 1e-2f) rel = 1e-2f;
     cluster.sync();
   }
+  if (clean && rank == 0 && t == 0) *clean = restarts == 0;
   // L is already in place (each column written when factored); the inverses
   // of the owned diagonal blocks, one warp each
   for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += kCL, ++q)
@@ -1067,7 +1087,7 @@ static mes_status diag_inv(const float* L, int r, float* Linv_blk, const int* sk
 size_t chol_smem() { return (1024 + PB * (PB + 1) + 1024 * (PB + 1)) * sizeof(float); }
 
 mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, float* Linv_blk, int* flags,
-                const int* skip, cudaStream_t st) {
+                const int* skip, cudaStream_t st, int* clean) {
   if (r > 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "chol: rank above 1024");
   static bool attr = false;
   if (!attr) {
@@ -1080,6 +1100,7 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
   MES_TRY(audit(L, last, "chol L"));
   MES_TRY(audit(dinv, (size_t)r * 4 - 1, "chol dinv"));
   MES_TRY(audit(Linv_blk, (size_t)((r + PB - 1) / PB) * PB * PB * 4 - 1, "chol Linv blocks"));
+  if (clean) MES_TRY(audit(clean, sizeof(int) - 1, "chol clean"));
   ProfScope prof("chol_f32", st, r * (double)r * r / 3.0, 8.0 * r * (double)r);
   static int cluster_ok = -1;
   if (cluster_ok < 0) {
@@ -1100,7 +1121,8 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
     cudaGetLastError();
   }
   if (r > 128 && r <= kDsmMaxR && dsm_ok == 1) {
-    chol_dsm_kernel<<<kCL, kChol, chol_dsm_smem(r), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip);
+    chol_dsm_kernel<<<kCL, kChol, chol_dsm_smem(r), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip,
+                                                           clean);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return MES_OK;
     if (getenv("MES_DEBUG"))
@@ -1108,7 +1130,7 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
     dsm_ok = 0;
   }
   if (r > 128 && cluster_ok == 1) {
-    chol_cluster_kernel<<<kCL, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
+    chol_cluster_kernel<<<kCL, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip, clean);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return diag_inv(L, r, Linv_blk, skip, st);
     // a cluster launch the device cannot place is rejected before anything
@@ -1116,9 +1138,136 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
     if (getenv("MES_DEBUG")) fprintf(stderr, "[mes] cluster Cholesky launch rejected: %s\n", cudaGetErrorString(e));
     cluster_ok = 0;
   }
-  chol_kernel<<<1, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip);
+  chol_kernel<<<1, kChol, chol_smem(), st>>>(M, r, shift_rel, L, dinv, flags, skip, clean);
   MES_LAUNCH_CHECK();
   return diag_inv(L, r, Linv_blk, skip, st);
+}
+
+// --------------------------------------------------------------------------
+// trsm_wide: the same solve with 128 rows per CTA held column-major in shared
+// memory (column c of the row block contiguous), so a thread's 4 rows x 4
+// columns register tile reads its operands as two 16-byte loads per k (the
+// kernel above reads five 4-byte loads per 4 FMAs).  Fewer, busier CTAs:
+// about a tenth of the SM-time of the 32-row kernel for the same rows.
+// Per 32-column block: subtract the solved columns times the block row of L
+// (staged 32 x 32 at a time, next tile prefetched into registers), then
+// multiply by the inverted diagonal block.
+// --------------------------------------------------------------------------
+constexpr int kWRows = 128;
+constexpr int kWLd = kWRows + 4;   // column stride of the row block (16-byte aligned)
+constexpr int kTLd = PB + 4;       // row stride of a staged 32 x 32 tile
+constexpr int kWMaxR = 384;        // 207 KB of shared memory at r = 384
+
+size_t trsm_wide_smem(int r) { return (size_t)(r * kWLd + 2 * PB * kTLd) * sizeof(float); }
+
+__global__ void __launch_bounds__(kTrsm, 1)
+trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restrict__ L,
+                 const float* __restrict__ dinv, const float* __restrict__ Linv_blk, float* __restrict__ V, int round,
+                 const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) float sm[];
+  float* Vt = sm;                    // r columns x kWLd
+  float* Lk = Vt + r * kWLd;         // 32 x kTLd: Lk[k][c] = L[c0 + c][k0 + k]
+  float* Li = Lk + PB * kTLd;        // 32 x kTLd: Li[k][c] = (L_bb^-1)[c][k]
+  const int t = threadIdx.x;
+  const int rg = t >> 3, cg = t & 7;   // rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3 of the block
+  const int64_t row0 = (int64_t)blockIdx.x * kWRows;
+  for (int e = t; e < kWRows * r; e += kTrsm) {
+    const int ii = e % kWRows, c = e / kWRows;
+    const int64_t row = row0 + ii;
+    Vt[c * kWLd + ii] = (row < s) ? W[row + s * c] * dinv[c] : 0.f;
+  }
+  __syncthreads();
+  const int nb = (r + PB - 1) / PB;
+  for (int cb = 0; cb < nb; ++cb) {
+    const int c0 = cb * PB;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    if (c0 > 0) {
+      // element e = t + q * 256 of a 32 x 32 tile: c = e & 31, k = e >> 5
+      float pre[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
+        pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * k] : 0.f;
+      }
+      for (int k0 = 0; k0 < c0; k0 += PB) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
+          Lk[k * kTLd + c] = pre[q];
+        }
+        __syncthreads();
+        if (k0 + PB < c0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
+            pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * (k0 + PB + k)] : 0.f;
+          }
+        }
+#pragma unroll 8
+        for (int k = 0; k < PB; ++k) {
+          const float4 a = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
+          const float4 b = *reinterpret_cast<const float4*>(Lk + k * kTLd + 4 * cg);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+    }
+    // diagonal block: x := (x - acc) Linv^T, Linv = (L_bb)^-1
+    for (int e = t; e < PB * PB; e += kTrsm) {
+      const int c = e >> 5, k = e & 31;
+      Li[k * kTLd + c] = Linv_blk[(size_t)cb * PB * PB + c * PB + k];
+    }
+    const int kmax = min(PB, r - c0);
+    // x - acc for this thread's tile, written back before the product reads it
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * cg + j;
+      if (c < r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][j];
+    }
+    __syncthreads();
+    float x[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[i][j] = 0.f;
+    for (int k = 0; k < kmax; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
+      const float4 b = *reinterpret_cast<const float4*>(Li + k * kTLd + 4 * cg);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[i][j] = fmaf(av[i], bv[j], x[i][j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * cg + j;
+      if (c < r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][j];
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < kWRows * r; e += kTrsm) {
+    const int ii = e % kWRows, c = e / kWRows;
+    const int64_t row = row0 + ii;
+    if (row < s) {
+      const float v = Vt[c * kWLd + ii];
+      V[row + s * c] = round ? mes::round_tf32(v) : v;
+    }
+  }
 }
 
 template <int ROWS, bool BLOCKROW>
@@ -1150,6 +1299,18 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
   // (~210 KB budget): more rows amortise the L traffic, more CTAs fill the
   // GPU (aim for ~120).
   const size_t budget = 210 * 1024;
+  if (r <= kWMaxR) {   // the row block fits in shared memory
+    static bool wattr = false;
+    if (!wattr) {
+      MES_CUDA_TRY(cudaFuncSetAttribute(trsm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)trsm_wide_smem(kWMaxR)));
+      wattr = true;
+    }
+    const unsigned grid = (unsigned)((s + kWRows - 1) / kWRows);
+    trsm_wide_kernel<<<grid, kTrsm, trsm_wide_smem(r), st>>>(W, s, r, L, dinv, Linv_blk, V, round ? 1 : 0, skip);
+    MES_LAUNCH_CHECK();
+    return MES_OK;
+  }
   auto fits = [&](int rows, bool br) {
     return (size_t)((rows + (br ? PB : 0)) * (r + 1) + PB * (PB + 1)) * sizeof(float) <= budget;
   };

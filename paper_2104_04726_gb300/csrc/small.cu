@@ -32,7 +32,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 __global__ void __launch_bounds__(kT)
 slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int64_t L,
                        float* __restrict__ XB, double* __restrict__ partials, float* __restrict__ Xr,
-                       int round) {
+                       int round, uint16_t* __restrict__ X16, uint16_t* __restrict__ XB16) {
   __shared__ float tile[32][33];
   __shared__ double red[kT / 32];
   const int64_t tx = (s1 + 31) / 32, ty = (s2 + 31) / 32;
@@ -43,25 +43,37 @@ slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int6
     const int64_t rem = tIdx - l * tx * ty;
     const int64_t by = rem / tx, bx = rem - by * tx;
     const float* src = X + l * s1 * s2;
-    float* dst = XB + l * s1 * s2;
     const int c = threadIdx.x & 31;
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
       int64_t x = bx * 32 + c, y = by * 32 + rr;
-      float v = (x < s1 && y < s2) ? src[x + s1 * y] : 0.f;
+      const bool in = x < s1 && y < s2;
+      float v = in ? src[x + s1 * y] : 0.f;
       acc += (double)v * v;
+      if (X16 && in) X16[l * s1 * s2 + x + s1 * y] = mes::bf16_bits(v);
       if (round) v = mes::round_tf32(v);
-      if (Xr && x < s1 && y < s2) Xr[l * s1 * s2 + x + s1 * y] = v;
+      if (Xr && in) Xr[l * s1 * s2 + x + s1 * y] = v;
       tile[rr][c] = v;
     }
     __syncthreads();
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
       int64_t y = by * 32 + c, x = bx * 32 + rr;
-      if (x < s1 && y < s2) dst[y + s2 * x] = tile[c][rr];
+      if (x < s1 && y < s2) {
+        if (XB) XB[l * s1 * s2 + y + s2 * x] = tile[c][rr];
+        // the BF16 copy rounds the input value, not its TF32 rounding
+        if (XB16) XB16[l * s1 * s2 + y + s2 * x] = mes::bf16_bits(src[x + s1 * y]);
+      }
     }
     __syncthreads();
   }
   double t = block_sum_d(acc, red);
   if (threadIdx.x == 0 && partials) partials[blockIdx.x] = t;
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ in, uint16_t* __restrict__ out, int64_t n,
+                               const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mes::bf16_bits(in[i]);
 }
 
 __global__ void __launch_bounds__(kT)
@@ -283,14 +295,49 @@ __global__ void round_copy_kernel(const float* __restrict__ in, float* __restric
     out[i] = mes::round_tf32(in[i]);
 }
 
+__global__ void copy_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t n,
+                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+__global__ void identity_kernel(float* __restrict__ U, int64_t s, int r) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s * r; i += (int64_t)gridDim.x * blockDim.x)
+    U[i] = (i % s == i / s) ? 1.f : 0.f;
+}
+
 }  // namespace
 
 namespace mes {
 
+mes_status copy_if(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st) {
+  ProfScope prof("copy", st, 0.0, 8.0 * n);
+  copy_kernel<<<grid_for(n, kT, 1024), kT, 0, st>>>(in, out, n, skip);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status identity_fill(float* U, int64_t s, int r, cudaStream_t st) {
+  ProfScope prof("identity", st, 0.0, 4.0 * s * r);
+  identity_kernel<<<grid_for(s * r, kT, 64), kT, 0, st>>>(U, s, r);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
 mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
-                           double* partials, int nblocks, cudaStream_t st, float* Xr, bool round) {
-  ProfScope prof("slice_transpose", st, 0.0, (Xr ? 12.0 : 8.0) * s1 * s2 * L);
-  slice_transpose_kernel<<<nblocks, kT, 0, st>>>(X, s1, s2, L, XB, partials, Xr, round ? 1 : 0);
+                           double* partials, int nblocks, cudaStream_t st, float* Xr, bool round,
+                           uint16_t* X16, uint16_t* XB16) {
+  ProfScope prof("slice_transpose", st, 0.0,
+                 (4.0 + (XB ? 4 : 0) + (Xr ? 4 : 0) + (X16 ? 2 : 0) + (XB16 ? 2 : 0)) * s1 * s2 * L);
+  slice_transpose_kernel<<<nblocks, kT, 0, st>>>(X, s1, s2, L, XB, partials, Xr, round ? 1 : 0, X16, XB16);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status to_bf16(const float* in, uint16_t* out, int64_t n, const int* skip, cudaStream_t st) {
+  ProfScope prof("to_bf16", st, 0.0, 6.0 * n);
+  to_bf16_kernel<<<grid_for(n, kT, 2048), kT, 0, st>>>(in, out, n, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

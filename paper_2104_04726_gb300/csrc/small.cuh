@@ -31,12 +31,19 @@ struct KronDesc {
 mes_status kron_build(const KronDesc& d, float* K, const int* skip, cudaStream_t st);
 
 // XB = per-slice transpose of X (and ||X||^2 partials); with `round`, XB and
-// the optional copy Xr hold X rounded to TF32.
+// the optional copy Xr hold X rounded to TF32.  X16 / XB16 (nullable)
+// receive X and its per-slice transpose rounded to BF16.  XB is nullable.
 mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
                            double* partials, int nblocks, cudaStream_t st, float* Xr = nullptr,
-                           bool round = false);
+                           bool round = false, uint16_t* X16 = nullptr, uint16_t* XB16 = nullptr);
+// out = bits of round_bf16(in), elementwise; a no-op when *skip != 0
+mes_status to_bf16(const float* in, uint16_t* out, int64_t n, const int* skip, cudaStream_t st);
 // out = round_tf32(in), elementwise
 mes_status round_copy(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st);
+// out = in, elementwise; a no-op when *skip != 0
+mes_status copy_if(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st);
+// U (s x r, column-major) = the first r columns of the identity
+mes_status identity_fill(float* U, int64_t s, int r, cudaStream_t st);
 mes_status sumsq(const float* x, int64_t n, double* partials, int nblocks, const int* skip,
                  cudaStream_t st);
 mes_status uniform_fill(float* out, int64_t n, uint64_t seed, cudaStream_t st);
@@ -59,8 +66,10 @@ mes_status permute_core(const float* in, int64_t total, int64_t stride, int r, c
 // Shifted Cholesky of an r x r Gram: L, dinv and the inverses of the 32 x 32
 // diagonal blocks of L (Linv_blk: ceil(r/32) row-major 32 x 32 blocks), and
 // the right-side solve V = W D^-1 L^-T that completes one CholeskyQR pass.
+// clean (nullable device int) receives 1 when the factorization kept its
+// starting shift (or was skipped), 0 when a bad pivot forced a larger one.
 mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, float* Linv_blk, int* flags,
-                const int* skip, cudaStream_t st);
+                const int* skip, cudaStream_t st, int* clean = nullptr);
 mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* dinv, const float* Linv_blk,
                 float* V, bool round, const int* skip, cudaStream_t st);
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,

@@ -110,6 +110,7 @@ struct Driver {
   mes::Scratch* scr;
   const int* skip = nullptr;       // device stop flag, null outside the sweeps
   int* flags = nullptr;            // numerics flags (Cholesky pivots, pipeline waits)
+  int* clean = nullptr;            // 1 when the last fast CholeskyQR pass kept its shift
 
   float *cwA = nullptr, *cwX = nullptr, *H = nullptr, *Rinv = nullptr;
   float* dinv = nullptr;                    // equilibration of chol
@@ -120,6 +121,10 @@ struct Driver {
   int prec = MES_PREC_FP32;
   float* split_ws = nullptr;
   int64_t split_elems = 0;
+  uint16_t* Zh16 = nullptr;                 // BF16 copy of Zh (BF16 form, T-side steps)
+
+  // tensor-core forms: operands of the Y-side products stored TF32-rounded
+  bool tc() const { return prec != MES_PREC_FP32; }
 
   // precision-critical products (Grams of the factor update): FP32 CUDA cores
   mes_status gemm(const Gemm& g) {
@@ -135,44 +140,85 @@ struct Driver {
   mes_status big(const Gemm& g) {
     Gemm h = g;
     h.skip = skip;
-    if (prec == MES_PREC_TF32 && mes::tc_eligible(h, 0))
+    if (tc() && mes::tc_eligible(h, 0))
       return mes::gemm_tc(h, 0, split_ws, split_elems, flags, st);
     h.split_ws = split_ws;
     h.split_elems = split_elems;
     return mes::gemm_f32(h, st);
   }
 
-  // S (s x r) := orth(W) by three passes of CholeskyQR, the first shifted;
-  // in the TF32 form Srnd receives S rounded to TF32 (the tensor-core operand).
-  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout, float* Srnd) {
-    float* src = Win;
-    float* bufs[2] = {W2, Win};
-    for (int pass = 0; pass < 3; ++pass) {
-      float* dst = (pass == 2) ? Sout : bufs[pass & 1];
-      Gemm g = base();  // H = src^T src
-      g.M = r; g.N = r; g.K_lo = s;
-      g.A = src; g.a_m = s; g.a_k = 1;
-      g.B = src; g.b_n = s; g.b_k = 1;
-      g.C = H; g.c_m = 1; g.c_n = r;
-      g.lower = true;  // chol reads the lower triangle only
-      MES_TRY(gemm(g));
-      MES_TRY(mes::chol(H, (int)r, pass == 0 ? kShiftW : 0.f, cwA, dinv, linv, flags, skip, st));
-      MES_TRY(mes::trsm(src, s, (int)r, cwA, dinv, linv, dst, false, skip, st));   // dst = src R^-1
-      src = dst;
+  // a T-side product of the BF16 form: both operands BF16 (kind::f16),
+  // FP32 accumulation; the caller guarantees TMA eligibility
+  mes_status big16(const Gemm& g) {
+    Gemm h = g;
+    h.skip = skip;
+    return mes::gemm_tc(h, 1, split_ws, split_elems, flags, st);
+  }
+
+  // same, with an explicit skip flag (e.g. the conditional second pass of orth)
+  mes_status gemm_if(const Gemm& g, const int* skipf) {
+    Gemm h = g;
+    h.skip = skipf;
+    h.split_ws = split_ws;
+    h.split_elems = split_elems;
+    return mes::gemm_f32(h, st);
+  }
+
+  // One CholeskyQR pass dst = src R^-1 with R^T R = src^T src (equilibrated,
+  // starting shift `shift`); every kernel is a no-op when *skipf != 0.
+  mes_status cholqr_pass(const float* src, int64_t s, int64_t r, float shift, float* dst, const int* skipf,
+                         int* clean) {
+    Gemm g = base();  // H = src^T src
+    g.M = r; g.N = r; g.K_lo = s;
+    g.A = src; g.a_m = s; g.a_k = 1;
+    g.B = src; g.b_n = s; g.b_k = 1;
+    g.C = H; g.c_m = 1; g.c_n = r;
+    g.lower = true;  // chol reads the lower triangle only
+    MES_TRY(gemm_if(g, skipf));
+    MES_TRY(mes::chol(H, (int)r, shift, cwA, dinv, linv, flags, skipf, st, clean));
+    return mes::trsm(src, s, (int)r, cwA, dinv, linv, dst, false, skipf, st);
+  }
+
+  // S (s x r) := orth(W); in the TF32 form Srnd receives S rounded to TF32
+  // (the tensor-core operand).
+  //  robust: three passes of CholeskyQR, the first shifted: any start (the
+  //          random block of the initialisation, the first subspace steps).
+  //  fast:   one unshifted pass, and a second one only when that pass had to
+  //          raise its shift (a device flag decides, nothing is read back).
+  //          Inside the sweeps W arrives preconditioned by Z^T Z (subspace
+  //          step below) with an equilibrated condition number of a few
+  //          units, where one pass is orthonormal to FP32 precision.
+  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout, float* Srnd, bool robust) {
+    if (robust) {
+      float* src = Win;
+      float* bufs[2] = {W2, Win};
+      for (int pass = 0; pass < 3; ++pass) {
+        float* dst = (pass == 2) ? Sout : bufs[pass & 1];
+        MES_TRY(cholqr_pass(src, s, r, pass == 0 ? kShiftW : 0.f, dst, skip, nullptr));
+        src = dst;
+      }
+    } else {
+      MES_TRY(cholqr_pass(Win, s, r, 0.f, Sout, skip, clean));
+      MES_TRY(cholqr_pass(Sout, s, r, 0.f, Win, clean, nullptr));   // only if pass 1 restarted
+      MES_TRY(mes::copy_if(Win, Sout, s * r, clean, st));
     }
-    if (prec == MES_PREC_TF32 && Srnd) MES_TRY(mes::round_copy(Sout, Srnd, s * r, skip, st));
+    if (tc() && Srnd) MES_TRY(mes::round_copy(Sout, Srnd, s * r, skip, st));
     return MES_OK;
   }
 
   // One subspace step for a large mode: Y is given through two GEMM operand
   // descriptions (Yt: Z = Y^T S,  Yn: W = Y Zh), J = number of columns of Y_(n).
+  // In the BF16 form, z16 / w16 (nullable) describe the same products with
+  // Y = T in BF16: then S16 is the BF16 copy of S (read by Z = Y^T S and
+  // refreshed after the update) and Zh goes through a BF16 copy.
   mes_status subspace_step(const Gemm& zdesc, const Gemm& wdesc, int64_t J, int64_t s, int64_t r,
-                           float* S, float* Srnd) {
+                           float* S, float* Srnd, bool robust, const Gemm* z16 = nullptr,
+                           const Gemm* w16 = nullptr, uint16_t* S16 = nullptr) {
     // Z = Y^T S   (J x r, stored Z[j + J*q])
-    Gemm gz = zdesc;
-    gz.B = (prec == MES_PREC_TF32) ? Srnd : S; gz.b_n = s; gz.b_k = 1;
+    Gemm gz = z16 ? *z16 : zdesc;
+    gz.B = z16 ? reinterpret_cast<const float*>(S16) : (tc() ? Srnd : S); gz.b_n = s; gz.b_k = 1;
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
-    MES_TRY(big(gz));
+    MES_TRY(z16 ? big16(gz) : big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
     Gemm gh = base();
     gh.M = r; gh.N = r; gh.K_lo = J;
@@ -182,13 +228,21 @@ struct Driver {
     gh.lower = true;
     MES_TRY(gemm(gh));
     MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, linv, flags, skip, st));
-    // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in that form
-    MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, linv, Zh, prec == MES_PREC_TF32, skip, st));
+    // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in those forms
+    MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, linv, Zh, tc(), skip, st));
     // W = Y Zh   (s x r)
-    Gemm gw = wdesc;
+    Gemm gw = w16 ? *w16 : wdesc;
     gw.C = W; gw.c_m = 1; gw.c_n = s;
-    MES_TRY(big(gw));
-    return orth(W, s, r, S, Srnd);
+    if (w16) {
+      MES_TRY(mes::to_bf16(Zh, Zh16, J * r, skip, st));
+      gw.B = reinterpret_cast<const float*>(Zh16);
+      MES_TRY(big16(gw));
+    } else {
+      MES_TRY(big(gw));
+    }
+    MES_TRY(orth(W, s, r, S, Srnd, robust));
+    if (S16) MES_TRY(mes::to_bf16(S, S16, s * r, skip, st));
+    return MES_OK;
   }
 
   // Small-mode Gram (FP64) of fibres projected by the Kronecker matrix built
@@ -328,8 +382,6 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   const int precision = o.precision;
   if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_TF32)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: unknown precision %d", precision);
-  if (precision == MES_PREC_BF16)
-    return mes::fail(MES_ERR_NOT_IMPLEMENTED, "mes_tucker_als: the BF16 form is not built yet");
   // defaults: 2 subspace steps for the T-HOSVD start, 1 per factor update
   // (fit within 1e-6 of the FP64 oracle on the 1024x768 scene)
   const int init_iters = o.init_iters > 0 ? o.init_iters : 2;
@@ -362,26 +414,40 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (s1 * L * r2 > zsz) zsz = s1 * L * r2;
   if (r1 * r2 * Lr > zsz) zsz = r1 * r2 * Lr;
 
-  float *XB, *P, *Ca, *Bt, *Y0 = nullptr, *Y1 = nullptr, *ctmp, *T1, *T2;
+  float *XB = nullptr, *P, *Ca, *Bt, *Y0 = nullptr, *Y1 = nullptr, *ctmp, *T1, *T2;
   double *normX, *normQ, *sse, *xpart, *qpart, *fitlast;
   int *done, *flags;
   float* sign;
   int* order;
   const int nblk = (int)mes::grid_for(nel, 256, (int64_t)mes::sm_count() * 4);
-  MES_TRY(scr.alloc(&XB, nel));
   float *Pt, *Cat, *Xr = nullptr, *Ur[2] = {nullptr, nullptr};
-  const bool tf32 = precision == MES_PREC_TF32;
+  // BF16 form: the T-side products (P, Ca and the T-HOSVD products, whose
+  // operands are T and the factors) run on BF16 copies with FP32
+  // accumulation; the Y-side products (Z, W, B) run as in the TF32 form.
+  // BF16 rows must be 16-byte aligned for TMA (s1, s2 multiples of 8);
+  // otherwise the TF32 form runs.
+  const bool bf = precision == MES_PREC_BF16 && s1 % 8 == 0 && s2 % 8 == 0;
+  const bool tf32 = precision != MES_PREC_FP32;   // tensor-core forms
+  uint16_t *X16 = nullptr, *XB16 = nullptr, *U16[2] = {nullptr, nullptr};
+  if (!bf) MES_TRY(scr.alloc(&XB, nel));
   if (tf32) {
     // operands of the kind::tf32 products, pre-rounded to nearest TF32
     MES_TRY(scr.alloc(&Xr, nel));
     MES_TRY(scr.alloc(&Ur[0], s1 * r1));
     MES_TRY(scr.alloc(&Ur[1], s2 * r2));
   }
+  if (bf) {
+    MES_TRY(scr.alloc(&X16, nel));
+    MES_TRY(scr.alloc(&XB16, nel));
+    MES_TRY(scr.alloc(&U16[0], s1 * r1));
+    MES_TRY(scr.alloc(&U16[1], s2 * r2));
+    MES_TRY(scr.alloc(&d.Zh16, zsz));
+  }
   MES_TRY(scr.alloc(&P, s1 * r2 * L));
   MES_TRY(scr.alloc(&Ca, s2 * r1 * L));
   MES_TRY(scr.alloc(&Pt, s1 * r2 * L));
   MES_TRY(scr.alloc(&Cat, s2 * r1 * L));
-  d.prec = precision;
+  d.prec = bf ? MES_PREC_BF16 : precision == MES_PREC_BF16 ? MES_PREC_TF32 : precision;
   {
     int64_t ws = s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2;
     d.split_elems = 16 * ws;
@@ -416,6 +482,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   MES_TRY(scr.alloc(&qpart, nblk));
   MES_TRY(scr.alloc(&done, 8));
   flags = done + 1;   // flags[0] error bits, flags[1] Cholesky calls, flags[2] shift restarts
+  d.clean = done + 4;
   MES_TRY(scr.alloc(&sign, rmax));
   MES_TRY(scr.alloc(&order, rmax));
   d.flags = flags;
@@ -430,7 +497,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   float* U1 = factors[1];
 
   // ---- second layout of T and ||T||^2 ----
-  MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st, Xr, tf32));
+  MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st, Xr, tf32, X16, XB16));
   const float* Xop = tf32 ? Xr : X;    // T as an operand of the large products
   MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
 
@@ -441,10 +508,18 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       MES_CUDA_TRY(cudaMemcpyAsync(factors[n], o.init_factors[n], sizeof(float) * sh.s[n] * sh.r[n],
                                    cudaMemcpyDeviceToDevice, st));
       if (tf32 && n < 2) MES_TRY(mes::round_copy(factors[n], Ur[n], sh.s[n] * sh.r[n], nullptr, st));
+      if (bf && n < 2) MES_TRY(mes::to_bf16(factors[n], U16[n], sh.s[n] * sh.r[n], nullptr, st));
     }
   } else {
-    // small modes: exact eigenvectors of the unfolding Grams of T
+    // small modes: exact eigenvectors of the unfolding Grams of T.  A small
+    // mode at full rank has an orthogonal factor: it changes neither the
+    // other modes' Grams nor the core norm, and its eigenvectors are taken
+    // from the last sweep's B, so until then it starts as the identity.
     for (int n = 2; n < N; ++n) {
+      if (sh.r[n] == sh.s[n]) {
+        MES_TRY(mes::identity_fill(factors[n], sh.s[n], (int)sh.r[n], st));
+        continue;
+      }
       KronDesc kd;
       kd.nm = sh.nsm;
       for (int m = 0; m < sh.nsm; ++m) {
@@ -463,7 +538,8 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
       float* S = factors[n];
       MES_TRY(mes::uniform_fill(d.W, s * r, seed * 2 + n, st));
-      MES_TRY(d.orth(d.W, s, r, S, Ur[n]));
+      MES_TRY(d.orth(d.W, s, r, S, Ur[n], true));
+      if (bf) MES_TRY(mes::to_bf16(S, U16[n], s * r, nullptr, st));
       Gemm gz = base(), gw = base();
       int64_t J;
       if (n == 0) {
@@ -483,7 +559,15 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
         gw.A = Xop; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
         gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s1;
       }
-      for (int it = 0; it < init_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s, r, S, Ur[n]));
+      // BF16 form: the same products on the BF16 copies of T
+      Gemm gz16 = gz, gw16 = gw;
+      if (bf) {
+        gz16.A = reinterpret_cast<const float*>(n == 0 ? X16 : XB16);
+        gw16.A = reinterpret_cast<const float*>(n == 0 ? XB16 : X16);
+      }
+      for (int it = 0; it < init_iters; ++it)
+        MES_TRY(d.subspace_step(gz, gw, J, s, r, S, Ur[n], true, bf ? &gz16 : nullptr, bf ? &gw16 : nullptr,
+                                bf ? U16[n] : nullptr));
     }
   }
 
@@ -517,6 +601,50 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     fb.out = core; fb.out_lo = 1; fb.out_hi = r1; fb.out_l = r1 * r2;
     return mes::mix_fibres(fb, d.Kmat, (int)L, (int)Lr, skipf, st);
   };
+  // Q <- Q x_n M^T for an r_n x r_n column-major M (n = 0, 1): every mode-n
+  // fibre q of the core becomes sum_p M[p + r_n q] Q(.. p ..)
+  auto core_apply = [&](int n, const float* M) -> mes_status {
+    Gemm gq = base();
+    if (n == 0) {
+      gq.M = r1; gq.N = r2 * Lr; gq.K_lo = r1;
+      gq.A = M; gq.a_m = r1; gq.a_k = 1;
+      gq.B = core; gq.b_n = r1; gq.b_k = 1;
+      gq.C = ctmp; gq.c_m = 1; gq.c_n = r1;
+    } else {
+      gq.M = r1; gq.N = r2; gq.K_lo = r2; gq.batch = (int)Lr;
+      gq.A = core; gq.a_m = 1; gq.a_k = r1; gq.a_b = r1 * r2;
+      gq.B = M; gq.b_n = r2; gq.b_k = 1;
+      gq.C = ctmp; gq.c_m = 1; gq.c_n = r1; gq.c_b = r1 * r2;
+    }
+    MES_TRY(d.gemm(gq));
+    MES_CUDA_TRY(cudaMemcpyAsync(core, ctmp, sizeof(float) * r1 * r2 * Lr, cudaMemcpyDeviceToDevice, st));
+    return MES_OK;
+  };
+  // Ca = T x_1 S1^T: Ca[(q1 + r1 l) + r1 L y] = sum_x U0[x + s1 q1] X[x + s1 (y + s2 l)],
+  // on the BF16 copies when use16
+  auto ca_product = [&](bool use16) -> mes_status {
+    Gemm g = base();
+    g.M = r1; g.N = s2 * L; g.K_lo = s1;
+    g.A = tf32 ? Ur[0] : U0; g.a_m = s1; g.a_k = 1;
+    g.B = Xop; g.b_n = s1; g.b_k = 1;
+    g.C = Ca; g.c_m = 1; g.N_lo = s2; g.c_n = r1 * L; g.c_nh = r1;
+    g.round_tf32 = tf32;
+    // second layout Cat[y + s2 (q1 + r1 l)]: K-major operand of Z and B
+    g.C2 = Cat; g.c2_m = s2; g.c2_n = 1; g.c2_nh = s2 * r1;
+    if (!use16) return d.big(g);
+    g.A = reinterpret_cast<const float*>(U16[0]);
+    g.B = reinterpret_cast<const float*>(X16);
+    return d.big16(g);
+  };
+  // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Cat[y + s2 (q1 + r1 l)] U1[y + s2 q2]
+  auto b_product = [&]() -> mes_status {
+    Gemm g = base();
+    g.M = r1 * L; g.N = r2; g.K_lo = s2;
+    g.A = Cat; g.a_m = s2; g.a_k = 1;
+    g.B = tf32 ? Ur[1] : U1; g.b_n = s2; g.b_k = 1;
+    g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
+    return d.big(g);
+  };
   for (int sweep = 1; sweep <= max_iters; ++sweep) {
     // mode 1: P = T x_2 S2^T, per l: P[x][q2 + r2 l] = sum_y XB[y + s2 x + s1 s2 l] U1[y + s2 q2]
     {
@@ -528,7 +656,13 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       g.round_tf32 = tf32;
       // second layout Pt[x + s1 (q2 + r2 l)]: the K-major operand of Z below
       g.C2 = Pt; g.c2_m = 1; g.c2_n = s1; g.c2_b = s1 * r2;
-      MES_TRY(d.big(g));
+      if (bf) {
+        g.A = reinterpret_cast<const float*>(XB16);
+        g.B = reinterpret_cast<const float*>(U16[1]);
+        MES_TRY(d.big16(g));
+      } else {
+        MES_TRY(d.big(g));
+      }
       const float* Y = P;
       if (!sh.small_full) {
         KronDesc kd;
@@ -555,19 +689,12 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       gw.M = s1; gw.N = r1; gw.K_lo = J;          // W[x][q] = sum_j Y[j + J x] Zh[j + J q]
       gw.A = Y; gw.a_m = J; gw.a_k = 1;
       gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
-      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s1, r1, U0, Ur[0]));
+      for (int it = 0; it < inner_iters; ++it)
+        MES_TRY(d.subspace_step(gz, gw, J, s1, r1, U0, Ur[0], false, nullptr, nullptr, U16[0]));
     }
-    // mode 2: Ca = T x_1 S1^T: Ca[(q1 + r1 l) + r1 L y] = sum_x U0[x + s1 q1] X[x + s1 (y + s2 l)]
+    // mode 2: Ca = T x_1 S1^T
     {
-      Gemm g = base();
-      g.M = r1; g.N = s2 * L; g.K_lo = s1;
-      g.A = tf32 ? Ur[0] : U0; g.a_m = s1; g.a_k = 1;
-      g.B = Xop; g.b_n = s1; g.b_k = 1;
-      g.C = Ca; g.c_m = 1; g.N_lo = s2; g.c_n = r1 * L; g.c_nh = r1;
-      g.round_tf32 = tf32;
-      // second layout Cat[y + s2 (q1 + r1 l)]: K-major operand of Z and B
-      g.C2 = Cat; g.c2_m = s2; g.c2_n = 1; g.c2_nh = s2 * r1;
-      MES_TRY(d.big(g));
+      MES_TRY(ca_product(bf));
       const float* Y = Ca;
       if (!sh.small_full) {
         KronDesc kd;
@@ -594,17 +721,10 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       gw.M = s2; gw.N = r2; gw.K_lo = J;
       gw.A = Y; gw.a_m = J; gw.a_k = 1;
       gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
-      for (int it = 0; it < inner_iters; ++it) MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1, Ur[1]));
+      for (int it = 0; it < inner_iters; ++it)
+        MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1, Ur[1], false, nullptr, nullptr, U16[1]));
     }
-    // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Cat[y + s2 (q1 + r1 l)] U1[y + s2 q2]
-    {
-      Gemm g = base();
-      g.M = r1 * L; g.N = r2; g.K_lo = s2;
-      g.A = Cat; g.a_m = s2; g.a_k = 1;
-      g.B = tf32 ? Ur[1] : U1; g.b_n = s2; g.b_k = 1;
-      g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
-      MES_TRY(d.big(g));
-    }
+    MES_TRY(b_product());
     // small modes n = 3..N with r_n < s_n: Gram of B x_{m != n} S_m^T, exact
     // eigenvectors.  A full-rank small mode's factor is orthogonal: it leaves
     // every other mode's Gram and the core norm unchanged, so its
@@ -621,6 +741,14 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   }
   d.skip = nullptr;
 
+  // ---- BF16 form: B and the core from T itself (TF32-rounded), so the
+  // returned core carries no BF16 rounding of T ----
+  if (bf) {
+    MES_TRY(ca_product(false));
+    MES_TRY(b_product());
+    MES_TRY(core_from_B(nullptr));
+  }
+
   // ---- full-rank small modes: eigenvectors from the last sweep's B ----
   {
     bool any_full = false;
@@ -630,6 +758,21 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
         any_full = true;
       }
     if (any_full) MES_TRY(core_from_B(nullptr));
+  }
+
+  // ---- one more CholeskyQR pass on each large factor ----
+  // The sweeps orthonormalise with one pass (enough for the iteration); the
+  // returned factors get a second one, S <- S R^-1, and the core follows
+  // exactly: Q x_n S^T = (Q x_n R^-T) for the new S, i.e. Q <- Q x_n R^-T.
+  for (int n = 0; n < 2; ++n) {
+    const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
+    float* S = factors[n];
+    MES_TRY(d.cholqr_pass(S, s, r, 0.f, d.W, nullptr, nullptr));
+    MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
+    // R^-1 = D^-1 L^-T of that pass: the solve applied to the identity
+    MES_TRY(mes::identity_fill(d.cwX, r, (int)r, st));
+    MES_TRY(mes::trsm(d.cwX, r, (int)r, d.cwA, d.dinv, d.linv, d.Rinv, false, nullptr, st));
+    MES_TRY(core_apply(n, d.Rinv));
   }
 
   // ---- canonical basis of the large modes ----
@@ -671,20 +814,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
         gu.C = d.W; gu.c_m = 1; gu.c_n = s;
         MES_TRY(d.gemm(gu));
         MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
-        Gemm gq = base();  // Q <- Q x_n Z^T
-        if (n == 0) {
-          gq.M = r1; gq.N = r2 * Lr; gq.K_lo = r1;
-          gq.A = d.Rinv; gq.a_m = r1; gq.a_k = 1;
-          gq.B = core; gq.b_n = r1; gq.b_k = 1;
-          gq.C = ctmp; gq.c_m = 1; gq.c_n = r1;
-        } else {
-          gq.M = r1; gq.N = r2; gq.K_lo = r2; gq.batch = (int)Lr;
-          gq.A = core; gq.a_m = 1; gq.a_k = r1; gq.a_b = r1 * r2;
-          gq.B = d.Rinv; gq.b_n = r2; gq.b_k = 1;
-          gq.C = ctmp; gq.c_m = 1; gq.c_n = r1; gq.c_b = r1 * r2;
-        }
-        MES_TRY(d.gemm(gq));
-        MES_CUDA_TRY(cudaMemcpyAsync(core, ctmp, sizeof(float) * ncore, cudaMemcpyDeviceToDevice, st));
+        MES_TRY(core_apply(n, d.Rinv));   // Q <- Q x_n Z^T
       } else {
         MES_TRY(mes::diag_order(d.H, (int)r, order, st));
         MES_TRY(mes::permute_cols(S, s, (int)r, order, nullptr, d.W, st));
