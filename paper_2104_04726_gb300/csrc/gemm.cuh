@@ -34,8 +34,9 @@ struct Gemm {
   // C is symmetric and its consumer reads only m >= n: tiles wholly above the
   // diagonal are not computed (their elements of C are left as they were).
   bool lower = false;
-  // Residual mode: instead of storing, accumulate sum((ref - alpha*AB)^2) in
-  // FP64; ref is addressed like C.  partials needs gemm_partials(g) doubles.
+  // Residual mode: accumulate sum((ref - alpha*AB)^2) in FP64 (and store
+  // alpha*AB to C when C is given, without accumulate or rounding); ref is
+  // addressed like C.  partials needs gemm_partials(g) doubles.
   const float* ref = nullptr;
   double* partials = nullptr;
   // Optional FP32 workspace for split-K (deterministic: partial tiles are

@@ -151,8 +151,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g, int splits,
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         if (mok[i] && nok[j]) {
-          float d = __ldg(g.ref + cb + moff[i] + noff[j]) - g.alpha * acc[i][j];
+          const float v = g.alpha * acc[i][j];
+          float d = __ldg(g.ref + cb + moff[i] + noff[j]) - v;
           s += (double)d * (double)d;
+          if (g.C) g.C[cb + moff[i] + noff[j]] = v;   // the product is stored too
         }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __shared__ double red[NT / 32];
@@ -245,10 +247,13 @@ mes_status launch(const mes::Gemm& g, dim3 grid, cudaStream_t st) {
   }
   const int64_t sms = mes::sm_count();
   int splits = 1;
-  if (!g.ref && g.split_ws) {
-    while (tiles * splits * 2 <= sms * 2 && nkt / (splits * 2) >= 8 &&
-           (int64_t)(splits * 2) * g.batch * g.M * g.N <= g.split_elems)
-      splits *= 2;
+  if (!g.ref && g.split_ws && tiles < sms) {
+    // one wave of CTAs (the register tile allows one per SM), at least 8
+    // K-tiles each
+    int64_t want = sms / tiles;
+    if (want > nkt / 8) want = nkt / 8;
+    while (want > 1 && want * g.batch * g.M * g.N > g.split_elems) --want;
+    splits = want > 1 ? (int)want : 1;
   }
   const int64_t per = (nkt + splits - 1) / splits;
   splits = (int)((nkt + per - 1) / per);

@@ -8,8 +8,10 @@
 //   warp 1    allocates BN TMEM columns; one thread issues tcgen05.mma
 //             (M=128, N=BN, K=32 bytes per instruction) and commits each
 //             stage back to its producer barrier;
-//   warps 2-5 epilogue: tcgen05.ld 32x32b of their 32 TMEM lanes, then the
-//             strided (two-level) store, accumulate or fused residual.
+//   warps 2-9 epilogue: two warps per 32-lane quarter of TMEM (the access
+//             rule of tcgen05.ld), each draining half of the BN columns;
+//             tcgen05.ld 32x32b, then the strided (two-level) store,
+//             accumulate or fused residual.
 // Kinds: kind::tf32 on FP32 data and kind::f16 on BF16 data.  Split-K over
 // grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
 // result is deterministic.  Every mbarrier wait is bounded (globaltimer,
@@ -24,7 +26,8 @@
 namespace {
 
 constexpr int BM = 128;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;   // 2 control warps + 8 epilogue warps
+constexpr int kEpiWarps = 8;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct TcArgs {
@@ -145,12 +148,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Offsets of consecutive output columns n, n+1, ... under the two-level
+// split n = n_lo + N_lo * n_hi (offset n_lo * s_n + n_hi * s_nh), walked
+// without a division per column.
+struct ColWalk {
+  int64_t nl, nh, off, N_lo, s_n, s_nh;
+  __device__ __forceinline__ ColWalk(int64_t n, int64_t N_lo_, int64_t s_n_, int64_t s_nh_)
+      : N_lo(N_lo_), s_n(s_n_), s_nh(s_nh_) {
+    nh = n / N_lo;
+    nl = n - nh * N_lo;
+    off = nl * s_n + nh * s_nh;
+  }
+  __device__ __forceinline__ void next() {
+    if (++nl == N_lo) {
+      nl = 0;
+      ++nh;
+      off = nh * s_nh;
+    } else {
+      off += s_n;
+    }
+  }
+};
+
 template <int KIND, int BN, int STAGES>
 struct Cfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int EPI = kEpiWarps * 32 * 33 * 4;   // epilogue transpose tile, one 32 x 33 per warp
+  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI;
+  static_assert(SMEM + 8 * kEpiWarps <= 232448, "dynamic + static shared memory above 227 KB");
   // idesc: D=F32 (bits 4-5 = 1); A/B format (bits 7-9, 10-12): TF32 = 2,
   // BF16 = 1; both K-major; N >> 3 at bit 17; M >> 4 at bit 24.
   static constexpr uint32_t FMT = KIND == 0 ? 2u : 1u;
@@ -170,7 +197,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   uint64_t* empty = full + STAGES;
   uint64_t* accum = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  __shared__ double red[4];
+  float* epi = reinterpret_cast<float*>(tiles + STAGES * C::STAGE + 256);
+  __shared__ double red[kEpiWarps];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
@@ -250,9 +278,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     if (!ok) atomicOr(args.err, 16);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int wq = warp & 3;
+    const int wq = warp & 3;                 // TMEM lane quarter = rows wq*32 .. wq*32+31
+    const int half = (warp - 2) >> 2;        // columns half*BN/2 .. (half+1)*BN/2 - 1
     const int64_t m = m0 + wq * 32 + lane;
-    const bool waited = mbar_wait(accum, 0);
+    // warp-uniform: the transposed stores below shuffle across the warp
+    const bool waited = __all_sync(0xffffffffu, mbar_wait(accum, 0));
     if (!waited && lane == 0) atomicOr(args.err, 32);
     tc_fence_after();
     const bool mok = m < args.M;
@@ -261,44 +291,101 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int64_t moff = ml * args.c_m + mh * args.c_mh + (int64_t)b * args.c_b;
     const int64_t moff2 = ml * args.c2_m + mh * args.c2_mh + (int64_t)b * args.c2_b;
     double sq = 0.0;
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    // Rows of this warp are TMEM lanes (one row per thread after tcgen05.ld).
+    // An output whose n index is contiguous goes through a 32 x 33 shared
+    // tile so that each store instruction writes 32 consecutive n of one row;
+    // an output with contiguous m is written directly (lanes = rows).
+    float* tile = epi + (warp - 2) * 32 * 33;
+    const bool c_ncontig = args.c_n == 1;
+    const bool c2_ncontig = args.C2 && args.c2_n == 1;
+    // writes val (this lane's row, 32 columns) through the tile: element
+    // (row i of the warp, n = n0 + c0 + lane) at base + row_off_i + col_off(n)
+    // with col_off(n) = (n mod N_lo) * s_n + (n div N_lo) * s_nh
+    auto store_rows = [&](const float (&val)[32], float* base, int64_t row_off, int64_t c0, int64_t s_n,
+                          int64_t s_nh, bool acc, bool rnd) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = val[j];
+      __syncwarp();
+      const int64_t n = n0 + c0 + lane;
+      const int64_t nh = n / N_lo, nl = n - nh * N_lo;
+      const int64_t col_off = nl * s_n + nh * s_nh;
+      for (int i = 0; i < 32; ++i) {
+        const int64_t off = __shfl_sync(0xffffffffu, row_off, i);
+        const int64_t mi = m0 + wq * 32 + i;
+        if (mi < args.M && n < args.N) {
+          float* p = base + off + col_off;
+          float v = tile[i * 33 + lane];
+          if (acc) v += *p;
+          if (rnd) v = mes::round_tf32(v);
+          *p = v;
+        }
+      }
+      __syncwarp();
+    };
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
-      if (!waited || !mok) continue;
+      if (!waited) continue;
       if (args.splits > 1) {
-        float* dst = args.split_ws + (((int64_t)split * args.batch + b) * args.M + m) * args.N;
+        float val[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t n = n0 + c0 + j;
-          if (n < args.N) dst[n] = __uint_as_float(v[j]);
-        }
+        for (int j = 0; j < 32; ++j) val[j] = __uint_as_float(v[j]);
+        const int64_t row_off = (((int64_t)split * args.batch + b) * args.M + m) * args.N;
+        store_rows(val, args.split_ws, row_off, c0, 1, N_lo, false, false);   // col_off = n
         continue;
       }
+      if constexpr (RESID) {
+        if (!mok) continue;
+        ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t n = n0 + c0 + j;
-        if (n >= args.N) continue;
-        const int64_t nh = n / N_lo, nl = n - nh * N_lo;
-        const float val = args.alpha * __uint_as_float(v[j]);
-        if (RESID) {
-          const float d = __ldg(args.ref + moff + nl * args.c_n + nh * args.c_nh) - val;
+        for (int j = 0; j < 32; ++j, cw.next()) {
+          if (n0 + c0 + j >= args.N) continue;
+          const float val = args.alpha * __uint_as_float(v[j]);
+          const float d = __ldg(args.ref + moff + cw.off) - val;
           sq += (double)d * (double)d;
-        } else {
-          float* p = args.C + moff + nl * args.c_n + nh * args.c_nh;
-          float v = args.accumulate ? *p + val : val;
-          if (args.round_out) v = mes::round_tf32(v);
-          *p = v;
-          if (args.C2) args.C2[moff2 + nl * args.c2_n + nh * args.c2_nh] = args.round_out ? mes::round_tf32(val) : val;
+          if (args.C) args.C[moff + cw.off] = val;   // the product is stored too
+        }
+        continue;
+      } else {
+        float val[32];
+  #pragma unroll
+        for (int j = 0; j < 32; ++j) val[j] = args.alpha * __uint_as_float(v[j]);
+        if (c_ncontig) {
+          store_rows(val, args.C, moff, c0, args.c_n, args.c_nh, args.accumulate != 0, args.round_out != 0);
+        } else if (mok) {
+          ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
+  #pragma unroll
+          for (int j = 0; j < 32; ++j, cw.next()) {
+            if (n0 + c0 + j >= args.N) continue;
+            float* p = args.C + moff + cw.off;
+            float w = args.accumulate ? *p + val[j] : val[j];
+            if (args.round_out) w = mes::round_tf32(w);
+            *p = w;
+          }
+        }
+        if (args.C2) {
+          if (c2_ncontig) {
+            store_rows(val, args.C2, moff2, c0, args.c2_n, args.c2_nh, false, args.round_out != 0);
+          } else if (mok) {
+            ColWalk cw(n0 + c0, N_lo, args.c2_n, args.c2_nh);
+  #pragma unroll
+            for (int j = 0; j < 32; ++j, cw.next()) {
+              if (n0 + c0 + j >= args.N) continue;
+              args.C2[moff2 + cw.off] = args.round_out ? mes::round_tf32(val[j]) : val[j];
+            }
+          }
         }
       }
     }
     if (RESID) {
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-      if (lane == 0) red[wq] = sq;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (wq == 0 && lane == 0) {
+      if (lane == 0) red[warp - 2] = sq;
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
+      if (warp == 2 && lane == 0) {
         const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        args.partials[bid] = red[0] + red[1] + red[2] + red[3];
+        double tot = 0.0;
+        for (int w = 0; w < kEpiWarps; ++w) tot += red[w];
+        args.partials[bid] = tot;
       }
     }
   }

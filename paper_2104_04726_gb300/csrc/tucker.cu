@@ -295,17 +295,18 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
     h.C = out; h.c_m = 1; h.c_n = s1;
     if (mes::tc_eligible(g, 0) && mes::tc_eligible(h, 0)) {
       MES_TRY(mes::gemm_tc(g, 0, nullptr, 0, err, st));
-      if (out) MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
       if (ref && sse) {
+        // one pass stores the product (when out is given) and accumulates the residual
         double* part = nullptr;
         const int64_t np = mes::gemm_partials(h) * 2 + 16;   // TC tiles are 128 x 128 or 128 x 256
         MES_TRY(scr.alloc(&part, np));
         MES_CUDA_TRY(cudaMemsetAsync(part, 0, np * sizeof(double), st));
         h.ref = ref;
-        h.C = nullptr;
         h.partials = part;
         MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
         MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
+      } else if (out) {
+        MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
       }
       return MES_OK;
     }
@@ -335,29 +336,18 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
   h.A = fac[0]; h.a_m = 1; h.a_k = s1;
   h.B = T2; h.b_n = r1; h.b_k = 1;
   h.C = out; h.c_m = 1; h.c_n = s1;
-  if (ref && sse && !out) {
+  if (ref && sse) {
+    // one pass stores the product (when out is given) and accumulates the residual
     double* part = nullptr;
     const int64_t np = mes::gemm_partials(h);
     MES_TRY(scr.alloc(&part, np));
     h.ref = ref;
-    h.C = nullptr;
     h.partials = part;
     MES_TRY(mes::gemm_f32(h, st));
     MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
     return MES_OK;
   }
-  MES_TRY(mes::gemm_f32(h, st));
-  if (ref && sse) {
-    // the residual is a second pass of the same product in residual mode
-    double* part = nullptr;
-    const int64_t np = mes::gemm_partials(h);
-    MES_TRY(scr.alloc(&part, np));
-    h.ref = ref;
-    h.partials = part;
-    MES_TRY(mes::gemm_f32(h, st));
-    MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
-  }
-  return MES_OK;
+  return mes::gemm_f32(h, st);
 }
 
 }  // namespace
