@@ -335,6 +335,77 @@ def measure_serving(mes, dev, precision, n_req, rate, seed, slots, budget_gb):
             "fp32_alone_ms": fp32}
 
 
+def measure_batch(mes, dev, precision, n_stacks, seed):
+    """Batched form: n_stacks stacks of the mixed workload (640x480, 1280x720
+    or 1920x1080; 3..7 exposures per view; ranks 20% of the two image modes,
+    full rank for colour and view x exposure; IPT or Y'CbCr; 20 sweeps;
+    16-bit quantiser) submitted as one captured CUDA graph and replayed,
+    beside the same stacks as sequential calls of the plain FP32 path on one
+    stream.  Reports both rates and the largest relative fit deviation of a
+    batched stack from its FP32 result."""
+    import numpy as np
+    import torch
+    import synth
+
+    rng = np.random.default_rng(seed)
+    stops = tuple(2.0 ** e for e in (-3, -2, -1, 0, 1, 2, 3))
+    scenes = {}
+    for s1, s2 in SERVE_SIZES:
+        spec = synth.SceneSpec(s1, s2, stops, views=2, d_max=max(4, s1 // 40))
+        scenes[(s1, s2)] = torch.from_numpy(synth.make_stack(spec, 6000 + s1)).to(dev)
+    draws = []
+    for _ in range(n_stacks):
+        s1, s2 = SERVE_SIZES[int(rng.integers(3))]
+        E = int(rng.integers(3, 8))
+        base = scenes[(s1, s2)]
+        Eb = base.shape[0] // 2
+        rgb = torch.cat([base[:E], base[Eb:Eb + E]]).contiguous()
+        draws.append(((s1, s2, 3, 2 * E), (round(0.2 * s1), round(0.2 * s2), 3, 2 * E), rgb,
+                      "ipt" if rng.random() < 0.5 else "ycbcr"))
+
+    def problems(prec):
+        return [mes.Problem(d, r, rgb8=rgb, space=sp, max_iters=20, tol=0.0, precision=prec, quant_bits=16)
+                for d, r, rgb, sp in draws]
+
+    probs = problems(precision)
+    st = torch.cuda.Stream(device=dev)   # graph capture needs a stream other than the legacy one
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    with torch.cuda.stream(st):
+        b = mes.Batch(16)
+        b.run(probs)                  # one-time setup outside the capture
+        st.synchronize()
+        b.capture(probs, stream=st)
+        b.launch()
+        st.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            b.launch()
+        e1.record(st)
+        st.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3 / reps
+        fits = [float(p.fit) for p in probs]
+        b.close()
+        p32 = problems("fp32")
+        b1 = mes.Batch(1)
+        b1.run(p32[:1])
+        st.synchronize()
+        e0.record(st)
+        for p in p32:
+            b1.run([p])
+        e1.record(st)
+        st.synchronize()
+        t_seq = e0.elapsed_time(e1) / 1e3
+        b1.close()
+    f32 = [float(p.fit) for p in p32]
+    dev_rel = max(abs(a - c) / abs(c) for a, c in zip(fits, f32))
+    return {"stacks": n_stacks, "precision": precision, "graph": True, "internal_streams": 16,
+            "stacks_per_s": n_stacks / t_batch, "ms_per_batch": 1e3 * t_batch,
+            "fp32_sequential_stacks_per_s": n_stacks / t_seq, "speedup_vs_fp32_sequential": t_seq / t_batch,
+            "max_rel_fit_dev_vs_fp32": dev_rel,
+            "fhd_equiv_stacks": sum(d[0][0] * d[0][1] * d[0][3] for d in draws) / (1920 * 1080 * 10)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,6 +421,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0 = skip it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving measurement")
+    ap.add_argument("--batch-stacks", type=int, default=64,
+                    help="stacks of the batched-form measurement (0 = skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -415,7 +488,7 @@ def main():
                 mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=precision,
                                outputs=(self.core, self.facs, self.fit, self.itd, None))
                 q, sc = mes.quantize_core(self.core, ranks, 16)
-                mes.reconstruct(self.core, self.facs, dims, ranks, ref=self.X)
+                mes.reconstruct(self.core, self.facs, dims, ranks, ref=self.X, precision=precision)
                 if e2e:
                     self.q_host.copy_(q, non_blocking=True)
                     self.s_host.copy_(sc, non_blocking=True)
@@ -520,6 +593,8 @@ def main():
             line["fp32_path"] = {"value": fp32["value"], "ms_per_step": fp32["ms_per_step"], "fit": fp32["fit"],
                                  "speedup": res["value"] / fp32["value"], "max_rel_fit_dev": dev_rel,
                                  "clocks": fp32["clocks"]}
+        if args.batch_stacks > 0 and world == 1:
+            line["batch"] = measure_batch(mes, dev, args.precision, args.batch_stacks, seed=11)
         if args.serve_requests > 0 and world == 1:
             line["serve"] = measure_serving(mes, dev, args.precision, args.serve_requests, args.serve_rate,
                                             seed=7, slots=8, budget_gb=96)

@@ -168,11 +168,18 @@ mes_status mes_tucker_als_workspace_size(int N, const int64_t* dims, const int64
  *                 receives sum((ref - out)^2) in FP64 (fused into the last
  *                 contraction; bitwise reproducible).
  *  sse      [out] nullable device double.
- * Same shape limits and errors as mes_tucker_als.
+ *  precision      MES_PREC_FP32: every product on CUDA cores in FP32;
+ *                 MES_PREC_TF32 or MES_PREC_BF16: the two large products on
+ *                 tensor cores with each operand split into two TF32 terms
+ *                 (hi*hi + hi*lo + lo*hi, FP32-level accuracy: about 3 * 2^-22
+ *                 relative per product); falls back to CUDA cores when r_1
+ *                 or r_2 is not a multiple of 4 (16-byte rows for TMA).
+ * Same shape limits and errors as mes_tucker_als; MES_ERR_INVALID_ARG for an
+ * unknown precision.
  */
 mes_status mes_reconstruct(const float* core, const float* const* factors, int N,
                            const int64_t* dims, const int64_t* ranks, float* out,
-                           const float* ref, double* sse, void* stream);
+                           const float* ref, double* sse, int precision, void* stream);
 
 /*
  * mes_quantize_core -- core quantiser, the rate knob of the scheme (the
@@ -363,7 +370,8 @@ mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, d
  * paper; used by the test suite to check each kernel in isolation).
  * C[b][m][n] = sum_k A[b][m][k] * B[b][n][k], all row-major FP32 device
  * arrays, batch >= 1.  impl 0: CUDA-core FP32 kernel; 1: tcgen05 kind::tf32;
- * 2: tcgen05 kind::f16 on BF16-rounded copies of A and B.  Synchronises the
+ * 2: tcgen05 kind::f16 on BF16-rounded copies of A and B; 3: tcgen05
+ * kind::tf32 on the three-term split (hi + lo of A and B).  Synchronises the
  * stream.  MES_ERR_INVALID_ARG for bad sizes or operands the tensor-core
  * kernel cannot address (row strides must be multiples of 16 bytes);
  * MES_ERR_TIMEOUT if a bounded pipeline wait gave up.

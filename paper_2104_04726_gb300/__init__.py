@@ -149,9 +149,12 @@ def tucker_als_workspace_size(dims: Sequence[int], ranks: Sequence[int], precisi
     return int(n.value)
 
 
-def reconstruct(core, factors, dims: Sequence[int], ranks: Sequence[int], out=None, ref=None):
+def reconstruct(core, factors, dims: Sequence[int], ranks: Sequence[int], out=None, ref=None,
+                precision: str = "fp32"):
     """T_hat = Q x_1 S^(1) ... x_N S^(N) (Eq. 1).  With `ref`, also returns
-    sum((ref - T_hat)^2) as a float64 CUDA scalar (fused)."""
+    sum((ref - T_hat)^2) as a float64 CUDA scalar (fused).  precision "fp32":
+    CUDA cores; "tf32"/"bf16": tensor cores with the three-term TF32 split
+    (FP32-level accuracy)."""
     torch = _torch()
     _need(core, torch.float32, "core")
     N = len(dims)
@@ -161,7 +164,7 @@ def reconstruct(core, factors, dims: Sequence[int], ranks: Sequence[int], out=No
     fac_arr = (ctypes.c_void_p * N)(*[f.data_ptr() for f in factors])
     lib = _lib.load()
     st = lib.mes_reconstruct(_ptr(core), fac_arr, N, _i64(dims), _i64(ranks), _ptr(out), _ptr(ref),
-                             _ptr(sse), _stream())
+                             _ptr(sse), PRECISIONS[precision], _stream())
     _lib.check(st, "mes_reconstruct")
     return (out, sse) if ref is not None else out
 

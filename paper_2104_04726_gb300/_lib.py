@@ -34,7 +34,7 @@ SIGNATURES = {
     "mes_tucker_als": (_c.c_int, [_p, _c.c_int, _i64p, _i64p, _c.c_int, _c.c_double, _p,
                                   _c.POINTER(_p), _p, _p, _p]),
     "mes_tucker_als_workspace_size": (_c.c_int, [_c.c_int, _i64p, _i64p, _p, _c.POINTER(_c.c_size_t)]),
-    "mes_reconstruct": (_c.c_int, [_p, _c.POINTER(_p), _c.c_int, _i64p, _i64p, _p, _p, _p, _p]),
+    "mes_reconstruct": (_c.c_int, [_p, _c.POINTER(_p), _c.c_int, _i64p, _i64p, _p, _p, _p, _c.c_int, _p]),
     "mes_quantize_core": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _c.c_int, _p]),
     "mes_dequantize_core": (_c.c_int, [_p, _p, _c.c_int, _i64p, _p, _p]),
     "mes_quantize_core_noalloc": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _p]),

@@ -22,6 +22,10 @@ struct Gemm {
   int64_t a_m = 0, a_k = 0, a_kh = 0, a_b = 0;
   const float* B = nullptr;
   int64_t b_n = 0, b_k = 0, b_kh = 0, b_b = 0;
+  // low parts of A and B for the three-term TF32 tensor-core product (kind 2
+  // of gemm_tc): A = A + A2 and B = B + B2, all four exactly TF32, same strides
+  const float* A2 = nullptr;
+  const float* B2 = nullptr;
   float* C = nullptr;
   int64_t M_lo = 0, c_m = 0, c_mh = 0, N_lo = 0, c_n = 0, c_nh = 0, c_b = 0;
   // optional second output (same values, another layout), strides as for C

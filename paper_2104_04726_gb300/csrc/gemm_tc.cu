@@ -12,7 +12,11 @@
 //             rule of tcgen05.ld), each draining half of the BN columns;
 //             tcgen05.ld 32x32b, then the strided (two-level) store,
 //             accumulate or fused residual.
-// Kinds: kind::tf32 on FP32 data and kind::f16 on BF16 data.  Split-K over
+// Kinds: kind::tf32 on FP32 data, kind::f16 on BF16 data, and the
+// three-term TF32 split (KIND 2): with A = A_hi + A_lo and B = B_hi + B_lo,
+// both terms exactly TF32, each K slice issues A_hi B_hi + A_hi B_lo +
+// A_lo B_hi into one accumulator (the dropped A_lo B_lo is ~2^-22 of the
+// product), so the result has FP32-level accuracy.  Split-K over
 // grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
 // result is deterministic.  Every mbarrier wait is bounded (globaltimer,
 // 2 s); a timeout sets an error bit and the CTA tears down normally.
@@ -20,8 +24,16 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
 #include "gemm.cuh"
 #include "gemm_tc.cuh"
+#include "small.cuh"
 
 namespace {
 
@@ -117,7 +129,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (KIND == 0) {
+  if (KIND != 1) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
@@ -174,20 +186,28 @@ template <int KIND, int BN, int STAGES>
 struct Cfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int EPI = kEpiWarps * 32 * 33 * 4;   // epilogue transpose tile, one 32 x 33 per warp
-  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI;
-  static_assert(SMEM + 8 * kEpiWarps <= 232448, "dynamic + static shared memory above 227 KB");
+  // KIND 2 stages the low parts after the high parts: A_hi, B_hi, A_lo, B_lo
+  static constexpr int STAGE = (KIND == 2 ? 2 : 1) * (A_BYTES + B_BYTES);
+  // the epilogue's transpose tiles (one 32 x 33 per drain warp) reuse the
+  // operand ring, which is idle once the accumulator is complete
+  static constexpr int EPI = kEpiWarps * 32 * 33 * 4;
+  static_assert(EPI <= STAGES * STAGE, "epilogue tiles must fit in the operand ring");
+  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  // KIND 0/1 fit two CTAs per SM (one CTA's epilogue overlaps the other's
+  // main loop); KIND 2 stages four tiles per slice and runs one
+  static constexpr int CTAS_PER_SM = KIND == 2 ? 1 : 2;
+  static_assert(CTAS_PER_SM * (SMEM + 8 * kEpiWarps + 1024) <= 233472, "shared memory per SM");
   // idesc: D=F32 (bits 4-5 = 1); A/B format (bits 7-9, 10-12): TF32 = 2,
   // BF16 = 1; both K-major; N >> 3 at bit 17; M >> 4 at bit 24.
-  static constexpr uint32_t FMT = KIND == 0 ? 2u : 1u;
+  static constexpr uint32_t FMT = KIND == 1 ? 1u : 2u;
   static constexpr uint32_t IDESC =
       (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
 template <int KIND, int BN, int STAGES, bool RESID>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, KIND == 2 ? 1 : 2)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ CUtensorMap mapA2, const __grid_constant__ CUtensorMap mapB2,
                const TcArgs args) {
   using C = Cfg<KIND, BN, STAGES>;
   if (args.skip && *args.skip) return;
@@ -197,7 +217,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   uint64_t* empty = full + STAGES;
   uint64_t* accum = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  float* epi = reinterpret_cast<float*>(tiles + STAGES * C::STAGE + 256);
+  float* epi = reinterpret_cast<float*>(tiles);   // used only after the accumulator is complete
   __shared__ double red[kEpiWarps];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -218,6 +238,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+    if (KIND == 2) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA2) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB2) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -242,11 +266,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
       const int kt = kt_begin + i;
       const int kh = kt / args.k_tiles_lo;
-      const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 0 ? 4 : 2));
+      const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
       uint8_t* sa = tiles + stage * C::STAGE;
       mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
       tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
       tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+      if (KIND == 2) {
+        uint8_t* sl = sa + C::A_BYTES + C::B_BYTES;
+        tma_load_4d(sl, &mapA2, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
+        tma_load_4d(sl + C::A_BYTES, &mapB2, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+      }
       if (++stage == STAGES) {
         stage = 0;
         phase ^= 1u;
@@ -268,6 +297,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)   // 4 x 32 bytes of K per 128-byte row
         mma<KIND>(tmem, da + 2 * kk, db + 2 * kk, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+      if (KIND == 2) {
+        const uint32_t sl = sa + C::A_BYTES + C::B_BYTES;
+        const uint64_t dal = sw128_desc(sl), dbl = sw128_desc(sl + C::A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          mma<KIND>(tmem, da + 2 * kk, dbl + 2 * kk, C::IDESC, 1u);   // A_hi B_lo
+          mma<KIND>(tmem, dal + 2 * kk, db + 2 * kk, C::IDESC, 1u);   // A_lo B_hi
+        }
+      }
       mma_commit(&empty[stage]);
       if (++stage == STAGES) {
         stage = 0;
@@ -435,7 +473,7 @@ mes_status get_encode() {
 // 4-D map {K_lo, rows, K_hi, batch} of a K-major operand.
 bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_t rows, int64_t K_hi,
               int64_t batch, int64_t s_row, int64_t s_kh, int64_t s_b, int box_rows) {
-  const int E = kind == 0 ? 4 : 2;
+  const int E = kind == 1 ? 2 : 4;
   cuuint64_t dims[4] = {(cuuint64_t)K_lo, (cuuint64_t)rows, (cuuint64_t)K_hi, (cuuint64_t)batch};
   int64_t st[3] = {s_row * E, s_kh * E, s_b * E};
   // unit dims get a harmless stride that keeps the strides increasing
@@ -447,7 +485,7 @@ bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_
   cuuint64_t strides[3] = {(cuuint64_t)st[0], (cuuint64_t)st[1], (cuuint64_t)st[2]};
   cuuint32_t box[4] = {(cuuint32_t)(128 / E), (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(map, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+  CUresult r = g_encode(map, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -455,8 +493,8 @@ bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_
 }
 
 template <int KIND, int BN, int STAGES>
-mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, dim3 grid, bool resid,
-                     cudaStream_t st) {
+mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& ma2, const CUtensorMap& mb2,
+                     const TcArgs& a, dim3 grid, bool resid, cudaStream_t st) {
   using C = Cfg<KIND, BN, STAGES>;
   static bool attr = false;
   if (!attr) {
@@ -467,9 +505,9 @@ mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs&
     attr = true;
   }
   if (resid)
-    tc_gemm_kernel<KIND, BN, STAGES, true><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a);
+    tc_gemm_kernel<KIND, BN, STAGES, true><<<grid, kThreads, C::SMEM, st>>>(ma, mb, ma2, mb2, a);
   else
-    tc_gemm_kernel<KIND, BN, STAGES, false><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a);
+    tc_gemm_kernel<KIND, BN, STAGES, false><<<grid, kThreads, C::SMEM, st>>>(ma, mb, ma2, mb2, a);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
@@ -479,7 +517,9 @@ mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs&
 namespace mes {
 
 bool tc_eligible(const Gemm& g, int kind) {
-  const int E = kind == 0 ? 4 : 2;
+  const int E = kind == 1 ? 2 : 4;
+  if (kind == 2 && (!g.A2 || !g.B2 || reinterpret_cast<uintptr_t>(g.A2) % 16 || reinterpret_cast<uintptr_t>(g.B2) % 16))
+    return false;
   if (g.a_k != 1 || g.b_k != 1) return false;
   if ((g.a_m * E) % 16 || (g.b_n * E) % 16) return false;
   if (g.K_hi > 1 && ((g.a_kh * E) % 16 || (g.b_kh * E) % 16)) return false;
@@ -490,17 +530,31 @@ bool tc_eligible(const Gemm& g, int kind) {
   return true;
 }
 
-mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_elems, int* err, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return MES_OK;
-  MES_TRY(get_encode());
-  if (!tc_eligible(g, kind)) return fail(MES_ERR_INVALID_ARG, "gemm_tc: operands not TMA/K-major eligible");
-  const int BK = 128 / (kind == 0 ? 4 : 2);
-  const int bn = g.N > 128 ? 256 : 128;
-  CUtensorMap ma, mb;
+}  // namespace mes
+
+namespace {
+
+// One launch of the product with tile width bn (128 or 256) and a split-K
+// factor; splits <= 0 picks the factor by the fill rule (split while the
+// tile grid covers less than the SMs and each split keeps >= 4 K-tiles).
+mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, float* split_ws,
+                       int64_t split_ws_elems, int* err, cudaStream_t st) {
+  using namespace mes;
+  const int BK = 128 / (kind == 1 ? 2 : 4);
+  if (kind == 2 || (bn != 128 && bn != 256)) bn = 128;   // KIND 2 has only the 128-wide tile
+  CUtensorMap ma, mb, ma2, mb2;
   const bool ab = g.batch > 1 && g.a_b != 0, bb = g.batch > 1 && g.b_b != 0;
   if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
       !make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh, g.b_b, bn))
     return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map rejected");
+  if (kind == 2) {
+    if (!make_map(&ma2, g.A2, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
+        !make_map(&mb2, g.B2, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh, g.b_b, bn))
+      return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map of a low part rejected");
+  } else {
+    ma2 = ma;
+    mb2 = mb;
+  }
   TcArgs a;
   a.M = g.M;
   a.N = g.N;
@@ -527,7 +581,10 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   const int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + bn - 1) / bn) * g.batch;
   int splits = 1;
   const int64_t sms = sm_count();
-  if (!g.ref && split_ws) {
+  if (want_splits > 0 && !g.ref &&
+      (want_splits == 1 || (split_ws && (int64_t)want_splits * g.batch * g.M * g.N <= split_ws_elems))) {
+    splits = want_splits;   // a tuned factor the workspace can hold
+  } else if (!g.ref && split_ws) {
     while (tiles * splits * 2 <= sms && a.k_tiles_total / (splits * 2) >= 4 &&
            (int64_t)(splits * 2) * g.batch * g.M * g.N <= split_ws_elems)
       splits *= 2;
@@ -539,16 +596,21 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   a.split_ws = split_ws;
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + bn - 1) / bn), (unsigned)(g.batch * splits));
   {
-    ProfScope prof(kind == 0 ? "gemm_tf32_tc" : "gemm_bf16_tc", st,
+    // algorithmic work of the product itself (KIND 2 executes three MMAs
+    // per K slice and reads both parts of each operand)
+    ProfScope prof(kind == 0 ? "gemm_tf32_tc" : kind == 1 ? "gemm_bf16_tc" : "gemm_tf32x3_tc", st,
                    2.0 * g.M * g.N * (double)g.K_lo * g.K_hi * g.batch,
-                   (kind == 0 ? 4.0 : 2.0) * g.batch * ((double)g.M + g.N) * g.K_lo * g.K_hi +
+                   (kind == 1 ? 2.0 : kind == 2 ? 8.0 : 4.0) * g.batch * ((double)g.M + g.N) * g.K_lo * g.K_hi +
                        4.0 * g.batch * g.M * (double)g.N);
+    const bool rs = g.ref != nullptr;
     if (kind == 0) {
-      if (bn == 256) MES_TRY((launch_tc<0, 256, 4>(ma, mb, a, grid, g.ref != nullptr, st)));
-      else MES_TRY((launch_tc<0, 128, 6>(ma, mb, a, grid, g.ref != nullptr, st)));
+      if (bn == 256) MES_TRY((launch_tc<0, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
+      else MES_TRY((launch_tc<0, 128, 3>(ma, mb, ma2, mb2, a, grid, rs, st)));
+    } else if (kind == 1) {
+      if (bn == 256) MES_TRY((launch_tc<1, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
+      else MES_TRY((launch_tc<1, 128, 3>(ma, mb, ma2, mb2, a, grid, rs, st)));
     } else {
-      if (bn == 256) MES_TRY((launch_tc<1, 256, 4>(ma, mb, a, grid, g.ref != nullptr, st)));
-      else MES_TRY((launch_tc<1, 128, 6>(ma, mb, a, grid, g.ref != nullptr, st)));
+      MES_TRY((launch_tc<2, 128, 3>(ma, mb, ma2, mb2, a, grid, rs, st)));
     }
   }
   if (splits > 1) {
@@ -558,6 +620,119 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
     MES_LAUNCH_CHECK();
   }
   return MES_OK;
+}
+
+// --------------------------------------------------------------------------
+// Tile autotuner.  Per product shape (kind, M, N, K, batch, operand
+// batching, residual mode) the tile width and the split-K factor are chosen
+// by timing every candidate once on the caller's stream the first time the
+// shape is met; the choice is kept for the process.  Enabled by MES_TUNE=1;
+// MES_TUNE_CACHE=<file> loads earlier choices and appends new ones, one
+// "key = bn splits" line each.  Never inside a stream capture, never for an
+// accumulating product (a candidate run would add to C) and never in
+// residual mode; those use the fill rule.
+// --------------------------------------------------------------------------
+struct TcChoice {
+  int bn, splits;
+};
+std::mutex g_tune_mu;
+std::unordered_map<std::string, TcChoice> g_tune;
+int g_tune_state = -1;   // -1 unread, 0 off, 1 on
+
+bool tuning_on() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_state < 0) {
+    const char* e = getenv("MES_TUNE");
+    g_tune_state = (e && e[0] == '1') ? 1 : 0;
+    const char* path = getenv("MES_TUNE_CACHE");
+    if (path) {
+      if (FILE* f = fopen(path, "r")) {
+        char line[256];
+        while (fgets(line, sizeof line, f)) {
+          char* eq = strstr(line, " = ");
+          TcChoice c;
+          if (eq && sscanf(eq + 3, "%d %d", &c.bn, &c.splits) == 2 && (c.bn == 128 || c.bn == 256) && c.splits >= 1)
+            g_tune[std::string(line, eq)] = c;
+        }
+        fclose(f);
+      }
+    }
+  }
+  return g_tune_state == 1 || !g_tune.empty();
+}
+
+std::string tune_key(const mes::Gemm& g, int kind) {
+  char buf[200];
+  snprintf(buf, sizeof buf, "k%d m%lld n%lld kl%lld kh%lld b%d ab%d bb%d", kind, (long long)g.M, (long long)g.N,
+           (long long)g.K_lo, (long long)g.K_hi, g.batch, g.a_b != 0 ? 1 : 0, g.b_b != 0 ? 1 : 0);
+  return buf;
+}
+
+}  // namespace
+
+namespace mes {
+
+mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_elems, int* err, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return MES_OK;
+  MES_TRY(get_encode());
+  if (!tc_eligible(g, kind)) return fail(MES_ERR_INVALID_ARG, "gemm_tc: operands not TMA/K-major eligible");
+  const int bn0 = (g.N > 128 && kind != 2) ? 256 : 128;   // KIND 2 stages four tiles: N = 128
+  if (g.accumulate || g.ref || !tuning_on()) return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
+  const std::string key = tune_key(g, kind);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end())
+      return gemm_tc_cfg(g, kind, it->second.bn, it->second.splits, split_ws, split_ws_elems, err, st);
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone || g_tune_state != 1) {
+    cudaGetLastError();
+    return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
+  }
+  // candidates: both tile widths (one for KIND 2) x split-K 1..16 (>= 4 K-tiles a split)
+  const int BK = 128 / (kind == 1 ? 2 : 4);
+  const int64_t kt = ((g.K_lo + BK - 1) / BK) * g.K_hi;
+  cudaEvent_t e0, e1;
+  MES_CUDA_TRY(cudaEventCreate(&e0));
+  MES_CUDA_TRY(cudaEventCreate(&e1));
+  TcChoice best{bn0, 1};
+  float best_ms = 1e30f;
+  const bool was_prof = prof_on();
+  for (int bn : {128, 256}) {
+    if (bn == 256 && (kind == 2 || g.N <= 128)) continue;
+    for (int sp = 1; sp <= 16; sp *= 2) {
+      if (sp > 1 && (!split_ws || kt / sp < 4 || (int64_t)sp * g.batch * g.M * g.N > split_ws_elems)) break;
+      cudaEventRecord(e0, st);
+      mes_status r = gemm_tc_cfg(g, kind, bn, sp, split_ws, split_ws_elems, err, st);
+      cudaEventRecord(e1, st);
+      if (r != MES_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return r;
+      }
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = TcChoice{bn, sp};
+      }
+      cudaGetLastError();
+    }
+  }
+  (void)was_prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    if (const char* path = getenv("MES_TUNE_CACHE"))
+      if (FILE* f = fopen(path, "a")) {
+        fprintf(f, "%s = %d %d\n", key.c_str(), best.bn, best.splits);
+        fclose(f);
+      }
+  }
+  // the result of the call: the chosen configuration, run last
+  return gemm_tc_cfg(g, kind, best.bn, best.splits, split_ws, split_ws_elems, err, st);
 }
 
 }  // namespace mes
@@ -579,12 +754,13 @@ __global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16_raw* 
 }  // namespace
 
 // Test hook: C[m*N + n] = sum_k A[m*K + k] * B[n*K + k] (both row-major,
-// K-major), through the CUDA-core kernel (impl 0), kind::tf32 (impl 1) or
-// kind::f16 on BF16-rounded inputs (impl 2).
+// K-major), through the CUDA-core kernel (impl 0), kind::tf32 (impl 1),
+// kind::f16 on BF16-rounded inputs (impl 2) or the three-term TF32 split of
+// A and B (impl 3).
 extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M,
                                         int64_t N, int64_t K, int batch, void* stream) {
   mes::clear_error();
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 2)
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 3)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_gemm_selftest: bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
@@ -614,7 +790,18 @@ extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B
     g.A = reinterpret_cast<const float*>(Ab);
     g.B = reinterpret_cast<const float*>(Bb);
   }
-  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : 1, ws, ws_elems, err, st));
+  if (impl == 3) {
+    float *Ah, *Al, *Bh, *Bl;
+    MES_TRY(scr.alloc(&Ah, batch * M * K));
+    MES_TRY(scr.alloc(&Al, batch * M * K));
+    MES_TRY(scr.alloc(&Bh, batch * N * K));
+    MES_TRY(scr.alloc(&Bl, batch * N * K));
+    MES_TRY(mes::split_tf32(A, Ah, Al, batch * M * K, st));
+    MES_TRY(mes::split_tf32(B, Bh, Bl, batch * N * K, st));
+    g.A = Ah; g.A2 = Al;
+    g.B = Bh; g.B2 = Bl;
+  }
+  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : impl == 2 ? 1 : 2, ws, ws_elems, err, st));
   int herr = 0;
   MES_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   MES_CUDA_TRY(cudaStreamSynchronize(st));

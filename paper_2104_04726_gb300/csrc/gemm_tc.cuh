@@ -5,7 +5,9 @@
 
 namespace mes {
 
-// kind: 0 = kind::tf32 on FP32 operands, 1 = kind::f16 on BF16 operands.
+// kind: 0 = kind::tf32 on FP32 operands, 1 = kind::f16 on BF16 operands,
+// 2 = three-term TF32 split (g.A/g.B the high parts, g.A2/g.B2 the low parts,
+// all TF32-exact; FP32-level accuracy).
 // True when both operands are K-major and satisfy the TMA alignment rules.
 bool tc_eligible(const Gemm& g, int kind);
 // split_ws (nullable) holds FP32 split-K partial tiles; err receives bit

@@ -69,6 +69,17 @@ slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int6
   if (threadIdx.x == 0 && partials) partials[blockIdx.x] = t;
 }
 
+__global__ void split_tf32_kernel(const float* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                                  int64_t n, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = in[i];
+    const float h = mes::round_tf32(x);
+    hi[i] = h;
+    lo[i] = mes::round_tf32(x - h);
+  }
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ in, uint16_t* __restrict__ out, int64_t n,
                                const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -331,6 +342,13 @@ mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, fl
   ProfScope prof("slice_transpose", st, 0.0,
                  (4.0 + (XB ? 4 : 0) + (Xr ? 4 : 0) + (X16 ? 2 : 0) + (XB16 ? 2 : 0)) * s1 * s2 * L);
   slice_transpose_kernel<<<nblocks, kT, 0, st>>>(X, s1, s2, L, XB, partials, Xr, round ? 1 : 0, X16, XB16);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status split_tf32(const float* in, float* hi, float* lo, int64_t n, cudaStream_t st, const int* skip) {
+  ProfScope prof("split_tf32", st, 0.0, 12.0 * n);
+  split_tf32_kernel<<<grid_for(n, kT, 2048), kT, 0, st>>>(in, hi, lo, n, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

@@ -36,6 +36,9 @@ mes_status kron_build(const KronDesc& d, float* K, const int* skip, cudaStream_t
 mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, float* XB,
                            double* partials, int nblocks, cudaStream_t st, float* Xr = nullptr,
                            bool round = false, uint16_t* X16 = nullptr, uint16_t* XB16 = nullptr);
+// hi = round_tf32(in), lo = round_tf32(in - hi): the two terms of the
+// three-term TF32 tensor-core product (x = hi + lo to ~2^-22 relative)
+mes_status split_tf32(const float* in, float* hi, float* lo, int64_t n, cudaStream_t st, const int* skip = nullptr);
 // out = bits of round_bf16(in), elementwise; a no-op when *skip != 0
 mes_status to_bf16(const float* in, uint16_t* out, int64_t n, const int* skip, cudaStream_t st);
 // out = round_tf32(in), elementwise

@@ -164,17 +164,25 @@ struct Driver {
     return mes::gemm_f32(h, st);
   }
 
+  // H = A^T A for a column-major s x r matrix A (the Grams of the factor
+  // update), FP32 on CUDA cores in every form; chol reads the lower triangle.
+  // (The three-term TF32 tensor-core product was tried here and failed the
+  // rank-520-of-600 scene, whose Z^T Z is too ill-conditioned for it.)
+  mes_status gram(const float* A, int64_t s, int64_t r, const int* skipf) {
+    Gemm g = base();
+    g.M = r; g.N = r; g.K_lo = s;
+    g.A = A; g.a_m = s; g.a_k = 1;
+    g.B = A; g.b_n = s; g.b_k = 1;
+    g.C = H; g.c_m = 1; g.c_n = r;
+    g.lower = true;
+    return gemm_if(g, skipf);
+  }
+
   // One CholeskyQR pass dst = src R^-1 with R^T R = src^T src (equilibrated,
   // starting shift `shift`); every kernel is a no-op when *skipf != 0.
   mes_status cholqr_pass(const float* src, int64_t s, int64_t r, float shift, float* dst, const int* skipf,
                          int* clean) {
-    Gemm g = base();  // H = src^T src
-    g.M = r; g.N = r; g.K_lo = s;
-    g.A = src; g.a_m = s; g.a_k = 1;
-    g.B = src; g.b_n = s; g.b_k = 1;
-    g.C = H; g.c_m = 1; g.c_n = r;
-    g.lower = true;  // chol reads the lower triangle only
-    MES_TRY(gemm_if(g, skipf));
+    MES_TRY(gram(src, s, r, skipf));
     MES_TRY(mes::chol(H, (int)r, shift, cwA, dinv, linv, flags, skipf, st, clean));
     return mes::trsm(src, s, (int)r, cwA, dinv, linv, dst, false, skipf, st);
   }
@@ -220,13 +228,7 @@ struct Driver {
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
     MES_TRY(z16 ? big16(gz) : big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
-    Gemm gh = base();
-    gh.M = r; gh.N = r; gh.K_lo = J;
-    gh.A = Z; gh.a_m = J; gh.a_k = 1;
-    gh.B = Z; gh.b_n = J; gh.b_k = 1;
-    gh.C = H; gh.c_m = 1; gh.c_n = r;
-    gh.lower = true;
-    MES_TRY(gemm(gh));
+    MES_TRY(gram(Z, J, r, skip));
     MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, linv, flags, skip, st));
     // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in those forms
     MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, linv, Zh, tc(), skip, st));
@@ -264,14 +266,27 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
                                 const float* ref, double* sse, mes::Scratch& scr, float* T1, float* T2,
                                 float* Kmat, cudaStream_t st, int prec = MES_PREC_FP32, int* err = nullptr) {
   const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
-  if (prec == MES_PREC_TF32) {
-    // tensor-core form: the same two products with K-major operands, reading
-    // transposed copies of S1 and S2 (S^T stored with the rank index fastest)
-    float *U0t, *U1t;
+  if (prec != MES_PREC_FP32 && r1 % 4 == 0 && r2 % 4 == 0) {
+    // tensor-core form: the same two products with K-major operands (the
+    // factors transposed to rank-fastest copies), every operand split into
+    // two TF32 terms and multiplied by the three-term product, which keeps
+    // FP32-level accuracy: a plain TF32 product would add ~1e-3 relative
+    // error to every entry of T_hat, more than the residual being measured
+    float *U0t, *U1t, *U0h, *U0l, *U1h, *U1l, *T1h, *T1l, *T2h, *T2l;
     MES_TRY(scr.alloc(&U0t, s1 * r1));
     MES_TRY(scr.alloc(&U1t, s2 * r2));
+    MES_TRY(scr.alloc(&U0h, s1 * r1));
+    MES_TRY(scr.alloc(&U0l, s1 * r1));
+    MES_TRY(scr.alloc(&U1h, s2 * r2));
+    MES_TRY(scr.alloc(&U1l, s2 * r2));
+    MES_TRY(scr.alloc(&T1h, r1 * r2 * L));
+    MES_TRY(scr.alloc(&T1l, r1 * r2 * L));
+    MES_TRY(scr.alloc(&T2h, r1 * s2 * L));
+    MES_TRY(scr.alloc(&T2l, r1 * s2 * L));
     MES_TRY(mes::slice_transpose(fac[0], s1, r1, 1, U0t, nullptr, 64, st));
     MES_TRY(mes::slice_transpose(fac[1], s2, r2, 1, U1t, nullptr, 64, st));
+    MES_TRY(mes::split_tf32(U0t, U0h, U0l, s1 * r1, st));
+    MES_TRY(mes::split_tf32(U1t, U1h, U1l, s2 * r2, st));
     KronDesc kd;
     kd.nm = sh.nsm;
     for (int m = 0; m < sh.nsm; ++m) {
@@ -283,18 +298,20 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
     fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
     fb.out = T1; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
     MES_TRY(mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st));
+    MES_TRY(mes::split_tf32(T1, T1h, T1l, r1 * r2 * L, st));
     Gemm g = Gemm();   // T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2t[q2 + r2 y]
     g.M = r1; g.N = s2; g.K_lo = r2; g.batch = (int)L;
-    g.A = T1; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
-    g.B = U1t; g.b_n = r2; g.b_k = 1; g.b_b = 0;
+    g.A = T1h; g.A2 = T1l; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
+    g.B = U1h; g.B2 = U1l; g.b_n = r2; g.b_k = 1; g.b_b = 0;
     g.C = T2; g.c_m = 1; g.c_n = r1; g.c_b = r1 * s2;
     Gemm h = Gemm();   // out[x + s1 n] = sum_q1 S1t[q1 + r1 x] T2[q1 + r1 n]
     h.M = s1; h.N = s2 * L; h.K_lo = r1;
-    h.A = U0t; h.a_m = r1; h.a_k = 1;
-    h.B = T2; h.b_n = r1; h.b_k = 1;
+    h.A = U0h; h.A2 = U0l; h.a_m = r1; h.a_k = 1;
+    h.B = T2h; h.B2 = T2l; h.b_n = r1; h.b_k = 1;
     h.C = out; h.c_m = 1; h.c_n = s1;
-    if (mes::tc_eligible(g, 0) && mes::tc_eligible(h, 0)) {
-      MES_TRY(mes::gemm_tc(g, 0, nullptr, 0, err, st));
+    if (mes::tc_eligible(g, 2) && mes::tc_eligible(h, 2)) {
+      MES_TRY(mes::gemm_tc(g, 2, nullptr, 0, err, st));
+      MES_TRY(mes::split_tf32(T2, T2h, T2l, r1 * s2 * L, st));
       if (ref && sse) {
         // one pass stores the product (when out is given) and accumulates the residual
         double* part = nullptr;
@@ -303,10 +320,10 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
         MES_CUDA_TRY(cudaMemsetAsync(part, 0, np * sizeof(double), st));
         h.ref = ref;
         h.partials = part;
-        MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
+        MES_TRY(mes::gemm_tc(h, 2, nullptr, 0, err, st));
         MES_TRY(mes::sum_doubles(part, np, sse, nullptr, st));
       } else if (out) {
-        MES_TRY(mes::gemm_tc(h, 0, nullptr, 0, err, st));
+        MES_TRY(mes::gemm_tc(h, 2, nullptr, 0, err, st));
       }
       return MES_OK;
     }
@@ -831,9 +848,12 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (fit) {
     const float* fac[8];
     for (int n = 0; n < N; ++n) fac[n] = factors[n];
-    // evaluated in FP32 in every form: a TF32 reconstruction would add its own
-    // rounding (~1e-3 relative per entry) to the residual being measured
-    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st, MES_PREC_FP32, flags));
+    // evaluated at FP32-level accuracy in every form: CUDA cores in the FP32
+    // form, the three-term TF32 tensor-core product in the tensor-core forms
+    // (a plain TF32 reconstruction would add ~1e-3 relative rounding per entry
+    // to the residual being measured)
+    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st,
+                                 tf32 ? MES_PREC_TF32 : MES_PREC_FP32, flags));
     MES_TRY(mes::final_fit(normX, sse, fit, st));
   }
   return MES_OK;
@@ -841,7 +861,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
 
 extern "C" mes_status mes_reconstruct(const float* core, const float* const* factors, int N,
                                       const int64_t* dims, const int64_t* ranks, float* out,
-                                      const float* ref, double* sse, void* stream) {
+                                      const float* ref, double* sse, int precision, void* stream) {
   mes::clear_error();
   Shape sh;
   MES_TRY(make_shape(N, dims, ranks, &sh, "mes_reconstruct"));
@@ -850,6 +870,8 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
     if (!factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: factors[%d] is null", n);
   if ((ref == nullptr) != (sse == nullptr))
     return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: ref and sse go together");
+  if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_TF32)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: unknown precision %d", precision);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
   {
@@ -865,7 +887,11 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
   MES_TRY(scr.alloc(&T1, sh.r1 * sh.r2 * sh.L));
   MES_TRY(scr.alloc(&T2, sh.r1 * sh.s2 * sh.L));
   MES_TRY(scr.alloc(&Kmat, 16384));
-  return mes_reconstruct_impl(sh, core, factors, out, ref, sse, scr, T1, T2, Kmat, st);
+  int* err = nullptr;
+  MES_TRY(scr.alloc(&err, 1));
+  MES_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  return mes_reconstruct_impl(sh, core, factors, out, ref, sse, scr, T1, T2, Kmat, st,
+                              precision == MES_PREC_FP32 ? MES_PREC_FP32 : MES_PREC_TF32, err);
 }
 
 extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,

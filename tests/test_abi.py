@@ -74,7 +74,8 @@ def test_validation_without_gpu(lib):
     assert lib.mes_quantize_core(fake, 2, _i64([4, 4]), 1, fake, fake, 0, None) == 1
     assert lib.mes_quantize_core(fake, 2, _i64([4, 4]), 17, fake, fake, 0, None) == 1
     assert lib.mes_quantize_core(None, 2, _i64([4, 4]), 8, fake, fake, 0, None) == 1
-    assert lib.mes_reconstruct(fake, facs, 4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), fake, fake, None, None) == 1
+    assert lib.mes_reconstruct(fake, facs, 4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), fake, fake, None, 0, None) == 1
+    assert lib.mes_reconstruct(fake, facs, 4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), fake, None, None, 9, None) == 1
 
 
 def _c_layout(struct, fields):

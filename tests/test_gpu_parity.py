@@ -292,12 +292,15 @@ def test_warm_start_from_oracle_factors(mes):
     assert float(res["fit"].cpu()) > ref.fit - 2e-6
 
 
-def test_reconstruct_matches_oracle(mes):
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_reconstruct_matches_oracle(mes, prec):
+    # fp32: CUDA cores; tf32: tensor cores with the three-term TF32 split of
+    # every operand (~3 * 2^-22 relative per product, FP32-level accuracy)
     cfg, img = _scene("small_64x48")
     T = colour.colour_convert(img, cfg["space"])
     res = _run(mes, T, cfg["ranks"], 3, 0.0)
     dims, ranks = T.shape, cfg["ranks"]
-    Xh, sse = mes.reconstruct(res["core"], res["factors"], dims, ranks, ref=to_torch(T))
+    Xh, sse = mes.reconstruct(res["core"], res["factors"], dims, ranks, ref=to_torch(T), precision=prec)
     torch.cuda.synchronize()
     core, Us = to_paper(res["core"]), factors_np(res)
     want = tucker.reconstruct(core, Us)
@@ -437,7 +440,7 @@ def test_precision_forms_against_oracle_xga(mes):
     X, _ = mes.colour_convert(torch.from_numpy(img).to(DEV), cfg["space"])
     for prec, tol in (("fp32", 1e-5), ("tf32", 1e-4), ("bf16", 1e-4)):
         res = mes.tucker_als(X, dims, cfg["ranks"], max_iters=cfg["iters"], tol=0.0, precision=prec)
-        Xh = mes.reconstruct(res["core"], res["factors"], dims, cfg["ranks"])
+        Xh = mes.reconstruct(res["core"], res["factors"], dims, cfg["ranks"], precision=prec)
         torch.cuda.synchronize()
         fit = float(res["fit"].cpu())
         Xg = to_paper(Xh)
