@@ -205,30 +205,39 @@ def _traffic(family):
     return None, None
 
 
+def _family_roof(f, peaks, peak_src, sms):
+    """Roofline of one kernel family from its profiled launches: tensor-core
+    products against the measured BF16 peak (x 0.5 for the TF32 kinds,
+    nominal ratio; sustained figure, as they run inside a long step), FP32
+    CUDA-core arithmetic against SMs x 128 lanes x 2 x max clock, everything
+    else against the measured HBM copy bandwidth."""
+    name = f["name"]
+    if "_tc" in name:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.0 if name.startswith("gemm_bf16") else 0.5)
+        achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{peak_src} bf16_tflops_sustained x {'1' if name.startswith('gemm_bf16') else '0.5 (tf32)'}"}
+    elif f["flops"] > 0 and f["bytes"] / max(f["flops"], 1) < 0.1:
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = f["flops"] / (f["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz')} MHz"}
+    else:
+        achieved = f["bytes"] / (f["ms"] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
+
+
 def _roofline(fams, peaks, peak_src, sms):
     total_ms = sum(f["ms"] for f in fams) or 1.0
     top = fams[0]
     traffic, note = _traffic(top["name"])
     per_launch = lambda x: x / max(top["launches"], 1)
-    if top["name"].startswith("gemm_tf32_tc") or top["name"].startswith("gemm_bf16_tc"):
-        # tensor-core product: TF32 peak = half the measured BF16 dense peak
-        # (nominal TF32:BF16 ratio 1:2); sustained figure (timed inside a long step)
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (0.5 if "tf32" in top["name"] else 1.0)
-        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"{peak_src} bf16_tflops_sustained x {'0.5 (tf32)' if 'tf32' in top['name'] else '1'}"}
-    elif top["flops"] > 0 and top["bytes"] / max(top["flops"], 1) < 0.1:
-        # CUDA-core FP32 arithmetic: ALU bound; peak = SMs x 128 FP32 lanes x 2 flop x max SM clock
-        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = top["flops"] / (top["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"derived: {sms} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz')} MHz"}
-    else:
-        achieved = top["bytes"] / (top["ms"] / 1e3) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "peak_source": f"{peak_src} hbm_gbs"}
-    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": traffic, "kernel": top["name"],
+    roof = _family_roof(top, peaks, peak_src, sms)
+    roof.update({"traffic": traffic, "kernel": top["name"],
                  "share": top["ms"] / total_ms, "launches": top["launches"],
                  "avg_launch_us": 1e3 * top["ms"] / max(top["launches"], 1),
                  "algorithmic_bytes_per_launch": per_launch(top["bytes"]),
@@ -236,6 +245,19 @@ def _roofline(fams, peaks, peak_src, sms):
     if note:
         roof["traffic_note"] = note
     return roof
+
+
+def _family_rooflines(fams, peaks, peak_src, sms, n=6):
+    """The same roofline for the n families with the largest time share."""
+    total_ms = sum(f["ms"] for f in fams) or 1.0
+    out = []
+    for f in fams[:n]:
+        r = _family_roof(f, peaks, peak_src, sms)
+        t, _ = _traffic(f["name"])
+        out.append({"kernel": f["name"], "share": round(f["ms"] / total_ms, 4), "bound": r["bound"],
+                    "achieved": round(r["achieved"], 3), "peak": r["peak"], "unit": r["unit"],
+                    "frac": round(r["frac"], 5), "traffic": t})
+    return out
 
 
 SERVE_SIZES = ((640, 480), (1280, 720), (1920, 1080))
@@ -581,7 +603,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
                 "data": "synthetic",
                 "config": _config(name, cfg, dims, ranks, args.precision, S, world),
-                "roofline": roof, "gpu_launches": int(res["launches_per_step"] * args.steps),
+                "roofline": roof, "rooflines": _family_rooflines(res["fams"], peaks, peak_src, sms),
+                "gpu_launches": int(res["launches_per_step"] * args.steps),
                 "clocks": res["clocks"],
                 "e2e": {"value": res["e2e"], "unit": "stacks/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},

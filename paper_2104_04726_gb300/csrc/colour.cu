@@ -100,14 +100,18 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
         }
         convert_pixel(P, lut_lin, lut_p, bytes[0], bytes[1], bytes[2], o[0][i], o[1][i], o[2][i]);
       }
+      // the 24 squares of this group summed in FP32, then one FP64 add
+      // (the FP64 rate is a small fraction of the FP32 rate on this GPU)
+      float part = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float4* dst = reinterpret_cast<float4*>(out + (c + 3 * k) * npix + p0);
         dst[0] = make_float4(o[c][0], o[c][1], o[c][2], o[c][3]);
         dst[1] = make_float4(o[c][4], o[c][5], o[c][6], o[c][7]);
 #pragma unroll
-        for (int i = 0; i < kPix; ++i) acc += (double)o[c][i] * (double)o[c][i];
+        for (int i = 0; i < kPix; ++i) part = fmaf(o[c][i], o[c][i], part);
       }
+      acc += (double)part;
     }
   } else {
     const int64_t total = npix * K;
@@ -120,7 +124,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
       out[(3 * k + 0) * npix + p] = c0;
       out[(3 * k + 1) * npix + p] = c1;
       out[(3 * k + 2) * npix + p] = c2;
-      acc += (double)c0 * c0 + (double)c1 * c1 + (double)c2 * c2;
+      acc += (double)fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
     }
   }
   if (partials) {

@@ -1167,8 +1167,7 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
   if (skip && *skip) return;
   extern __shared__ __align__(16) float sm[];
   float* Vt = sm;                    // r columns x kWLd
-  float* Lk = Vt + r * kWLd;         // 32 x kTLd: Lk[k][c] = L[c0 + c][k0 + k]
-  float* Li = Lk + PB * kTLd;        // 32 x kTLd: Li[k][c] = (L_bb^-1)[c][k]
+  float* Lk = Vt + r * kWLd;         // 2 x 32 x kTLd: staged tiles, [k][c]
   const int t = threadIdx.x;
   const int rg = t >> 3, cg = t & 7;   // rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3 of the block
   const int64_t row0 = (int64_t)blockIdx.x * kWRows;
@@ -1202,7 +1201,38 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
     }
   }
   __syncthreads();
+  // The rows of the block are private to a warp (thread t owns rows
+  // 4 (t >> 3) .. +3, so each warp owns 16 rows): only the staged 32 x 32
+  // tiles are shared, and those go through a double buffer with one barrier
+  // per tile.  Block cb consumes the tiles L[c0 .. c0+31][32 j .. 32 j + 31]
+  // for j < cb, then (L_bb)^-1, all in one stream of tiles.
   const int nb = (r + PB - 1) / PB;
+  // tile q of the stream: (block, j); j == block means the inverted diagonal block
+  auto tile_load = [&](int cbq, int j, float (&pre)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * kTrsm;
+      if (j < cbq) {   // Lk[k][c] = L[c0 + c][32 j + k]
+        const int c = e & 31, k = e >> 5;
+        pre[q] = (PB * cbq + c < r) ? L[(PB * cbq + c) + (int64_t)r * (PB * j + k)] : 0.f;
+      } else {         // Li[k][c] = (L_bb^-1)[c][k]
+        const int c = e >> 5, k = e & 31;
+        pre[q] = Linv_blk[(size_t)cbq * PB * PB + c * PB + k];
+      }
+    }
+  };
+  auto tile_store = [&](float* buf, int cbq, int j, const float (&pre)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * kTrsm;
+      if (j < cbq) buf[(e >> 5) * kTLd + (e & 31)] = pre[q];
+      else buf[(e & 31) * kTLd + (e >> 5)] = pre[q];
+    }
+  };
+  float pre[4];
+  int cbn = 0, jn = 0;   // next tile to load
+  tile_load(cbn, jn, pre);
+  int bsel = 0;
   for (int cb = 0; cb < nb; ++cb) {
     const int c0 = cb * PB;
     float acc[4][4];
@@ -1210,80 +1240,64 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    if (c0 > 0) {
-      // element e = t + q * 256 of a 32 x 32 tile: c = e & 31, k = e >> 5
-      float pre[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
-        pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * k] : 0.f;
-      }
-      for (int k0 = 0; k0 < c0; k0 += PB) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
-          Lk[k * kTLd + c] = pre[q];
-        }
-        __syncthreads();
-        if (k0 + PB < c0) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int e = t + q * kTrsm, c = e & 31, k = e >> 5;
-            pre[q] = (c0 + c < r) ? L[(c0 + c) + (int64_t)r * (k0 + PB + k)] : 0.f;
-          }
-        }
+    for (int j = 0; j <= cb; ++j) {
+      float* buf = Lk + bsel * (PB * kTLd);
+      tile_store(buf, cb, j, pre);
+      __syncthreads();   // tile visible; every thread is done with the other buffer
+      // prefetch the next tile of the stream into registers
+      if (++jn > cbn) { ++cbn; jn = 0; }
+      if (cbn < nb) tile_load(cbn, jn, pre);
+      if (j < cb) {
+        const int k0 = PB * j;
 #pragma unroll 8
         for (int k = 0; k < PB; ++k) {
-          const float4 a = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
-          const float4 b = *reinterpret_cast<const float4*>(Lk + k * kTLd + 4 * cg);
-          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+          const float4 av = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
+          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a4[i], b4[jj], acc[i][jj]);
         }
-        __syncthreads();
+      } else {
+        // diagonal block: x := (x - acc) Linv^T; the rows are this warp's own
+        const int kmax = min(PB, r - c0);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int c = c0 + 4 * cg + jj;
+          if (c < r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][jj];
+        }
+        __syncwarp();
+        float x[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) x[i][jj] = 0.f;
+        for (int k = 0; k < kmax; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
+          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) x[i][jj] = fmaf(a4[i], b4[jj], x[i][jj]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int c = c0 + 4 * cg + jj;
+          if (c < r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][jj];
+        }
+        __syncwarp();
       }
+      bsel ^= 1;
     }
-    // diagonal block: x := (x - acc) Linv^T, Linv = (L_bb)^-1
-    for (int e = t; e < PB * PB; e += kTrsm) {
-      const int c = e >> 5, k = e & 31;
-      Li[k * kTLd + c] = Linv_blk[(size_t)cb * PB * PB + c * PB + k];
-    }
-    const int kmax = min(PB, r - c0);
-    // x - acc for this thread's tile, written back before the product reads it
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + 4 * cg + j;
-      if (c < r)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][j];
-    }
-    __syncthreads();
-    float x[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) x[i][j] = 0.f;
-    for (int k = 0; k < kmax; ++k) {
-      const float4 a = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
-      const float4 b = *reinterpret_cast<const float4*>(Li + k * kTLd + 4 * cg);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) x[i][j] = fmaf(av[i], bv[j], x[i][j]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + 4 * cg + j;
-      if (c < r)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][j];
-    }
-    __syncthreads();
   }
+  __syncthreads();
   if ((s & 3) == 0 && row0 + kWRows <= s && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
     for (int e = t; e < r * (kWRows / 4); e += kTrsm) {
       const int c = e >> 5;

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g, int splits,
     return;
   }
   if (RESID) {
-    double s = 0.0;
+    // the thread's 64 squares summed in FP32, one FP64 value per thread
+    float sf = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -153,9 +154,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const mes::Gemm g, int splits,
         if (mok[i] && nok[j]) {
           const float v = g.alpha * acc[i][j];
           float d = __ldg(g.ref + cb + moff[i] + noff[j]) - v;
-          s += (double)d * (double)d;
+          sf = fmaf(d, d, sf);
           if (g.C) g.C[cb + moff[i] + noff[j]] = v;   // the product is stored too
         }
+    double s = sf;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __shared__ double red[NT / 32];
     if ((t & 31) == 0) red[t >> 5] = s;

@@ -374,15 +374,37 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
       if constexpr (RESID) {
         if (!mok) continue;
-        ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
+        // 32 squares summed in FP32 (relative error ~32 * 2^-24 of a
+        // non-negative sum), then one FP64 add per chunk: GB300's FP64
+        // rate is a small fraction of its FP32 rate
+        float sqf = 0.f;
+        if (N_lo >= args.N) {
+          // one-level n: linear offsets, so the 32 reference loads are
+          // independent and go out together
+          const float* rp = args.ref + moff + (n0 + c0) * args.c_n;
+          float refv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j, cw.next()) {
-          if (n0 + c0 + j >= args.N) continue;
-          const float val = args.alpha * __uint_as_float(v[j]);
-          const float d = __ldg(args.ref + moff + cw.off) - val;
-          sq += (double)d * (double)d;
-          if (args.C) args.C[moff + cw.off] = val;   // the product is stored too
+          for (int j = 0; j < 32; ++j) refv[j] = (n0 + c0 + j < args.N) ? __ldg(rp + j * args.c_n) : 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (n0 + c0 + j >= args.N) continue;
+            const float val = args.alpha * __uint_as_float(v[j]);
+            const float d = refv[j] - val;
+            sqf = fmaf(d, d, sqf);
+            if (args.C) args.C[moff + (n0 + c0 + j) * args.c_n] = val;   // the product is stored too
+          }
+        } else {
+          ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
+#pragma unroll
+          for (int j = 0; j < 32; ++j, cw.next()) {
+            if (n0 + c0 + j >= args.N) continue;
+            const float val = args.alpha * __uint_as_float(v[j]);
+            const float d = __ldg(args.ref + moff + cw.off) - val;
+            sqf = fmaf(d, d, sqf);
+            if (args.C) args.C[moff + cw.off] = val;   // the product is stored too
+          }
         }
+        sq += (double)sqf;
         continue;
       } else {
         float val[32];
@@ -676,7 +698,10 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return MES_OK;
   MES_TRY(get_encode());
   if (!tc_eligible(g, kind)) return fail(MES_ERR_INVALID_ARG, "gemm_tc: operands not TMA/K-major eligible");
-  const int bn0 = (g.N > 128 && kind != 2) ? 256 : 128;   // KIND 2 stages four tiles: N = 128
+  // tile width: KIND 2 stages four tiles and has only N = 128; otherwise the
+  // width that pads N least (ties to 256: fewer re-reads of the A tile)
+  int bn0 = 128;
+  if (kind != 2 && g.N > 128) bn0 = ((g.N + 255) / 256) * 256 <= ((g.N + 127) / 128) * 128 ? 256 : 128;
   if (g.accumulate || g.ref || !tuning_on()) return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
   const std::string key = tune_key(g, kind);
   {

@@ -44,23 +44,24 @@ slice_transpose_kernel(const float* __restrict__ X, int64_t s1, int64_t s2, int6
     const int64_t by = rem / tx, bx = rem - by * tx;
     const float* src = X + l * s1 * s2;
     const int c = threadIdx.x & 31;
+    float part = 0.f;   // this tile's squares in FP32, one FP64 add per tile
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
       int64_t x = bx * 32 + c, y = by * 32 + rr;
       const bool in = x < s1 && y < s2;
       float v = in ? src[x + s1 * y] : 0.f;
-      acc += (double)v * v;
+      part = fmaf(v, v, part);
       if (X16 && in) X16[l * s1 * s2 + x + s1 * y] = mes::bf16_bits(v);
-      if (round) v = mes::round_tf32(v);
-      if (Xr && in) Xr[l * s1 * s2 + x + s1 * y] = v;
-      tile[rr][c] = v;
+      if (Xr && in) Xr[l * s1 * s2 + x + s1 * y] = round ? mes::round_tf32(v) : v;
+      tile[rr][c] = v;   // the input value: each output rounds it its own way
     }
+    acc += (double)part;
     __syncthreads();
     for (int rr = threadIdx.x >> 5; rr < 32; rr += kT / 32) {
       int64_t y = by * 32 + c, x = bx * 32 + rr;
       if (x < s1 && y < s2) {
-        if (XB) XB[l * s1 * s2 + y + s2 * x] = tile[c][rr];
-        // the BF16 copy rounds the input value, not its TF32 rounding
-        if (XB16) XB16[l * s1 * s2 + y + s2 * x] = mes::bf16_bits(src[x + s1 * y]);
+        const float v = tile[c][rr];
+        if (XB) XB[l * s1 * s2 + y + s2 * x] = round ? mes::round_tf32(v) : v;
+        if (XB16) XB16[l * s1 * s2 + y + s2 * x] = mes::bf16_bits(v);
       }
     }
     __syncthreads();
@@ -92,11 +93,20 @@ sumsq_kernel(const float* __restrict__ x, int64_t n, double* __restrict__ partia
              const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double red[kT / 32];
+  // runs of 16 squares summed in FP32, one FP64 add per run
   double acc = 0.0;
+  float part = 0.f;
+  int run = 0;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    double v = x[i];
-    acc += v * v;
+    const float v = x[i];
+    part = fmaf(v, v, part);
+    if (++run == 16) {
+      acc += (double)part;
+      part = 0.f;
+      run = 0;
+    }
   }
+  acc += (double)part;
   double t = block_sum_d(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
