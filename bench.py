@@ -7,11 +7,14 @@ quantiser (16 bits) and reconstruction with the fused residual.  The metric
 is stacks per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--precision tf32|fp32] [--stacks S] [--no-fp32-path]
+                  [--precision bf16|tf32|fp32] [--stacks S] [--no-fp32-path]
+                  [--batch-stacks B] [--serve-requests R] [--serve-rate RATE]
 
-The default times the TF32 tensor-core form over 8 concurrent stacks per step
-and, beside it, the plain FP32 path on the same stacks (its stacks/s and the
-largest relative fit deviation between the two).
+The default times the BF16 form over 16 concurrent stacks per step and,
+beside it, the plain FP32 path on the same stacks (its stacks/s and the
+largest relative fit deviation between the two), then the batched form (64
+mixed stacks as one CUDA graph) and the served form (a Poisson request
+stream through the serving loop, p50/p99 latency).
 
 Multi-GPU (torchrun, one rank per GPU): every rank decomposes its own stacks
 (independent problems, weak scaling, no collective on the data path); the
@@ -434,12 +437,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mes", choices=["mes", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["fp32", "bf16", "tf32"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true",
                     help="skip timing the plain FP32 path beside the chosen precision form")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--stacks", type=int, default=8, help="independent stacks per step, one CUDA stream each")
+    ap.add_argument("--stacks", type=int, default=16, help="independent stacks per step, one CUDA stream each")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving measurement (0 = skip it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving measurement")

@@ -1144,23 +1144,27 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
 }
 
 // --------------------------------------------------------------------------
-// trsm_wide: the same solve with 128 rows per CTA held column-major in shared
-// memory (column c of the row block contiguous), so a thread's 4 rows x 4
-// columns register tile reads its operands as two 16-byte loads per k (the
-// kernel above reads five 4-byte loads per 4 FMAs).  Fewer, busier CTAs:
-// about a tenth of the SM-time of the 32-row kernel for the same rows.
+// trsm_wide: the same solve with NT / 2 rows per CTA (NT threads) held
+// column-major in shared memory (column c of the row block contiguous), so a
+// thread's 4 rows x 4 columns register tile reads its operands as two
+// 16-byte loads per k (the kernel above reads five 4-byte loads per 4 FMAs).
+// With NT = 128 (64 rows, 113 KB at r = 384) two CTAs share an SM, so one
+// CTA's barrier and shared-memory waits overlap the other's FMAs.
 // Per 32-column block: subtract the solved columns times the block row of L
 // (staged 32 x 32 at a time, next tile prefetched into registers), then
 // multiply by the inverted diagonal block.
 // --------------------------------------------------------------------------
-constexpr int kWRows = 128;
-constexpr int kWLd = kWRows + 4;   // column stride of the row block (16-byte aligned)
-constexpr int kTLd = PB + 4;       // row stride of a staged 32 x 32 tile
-constexpr int kWMaxR = 384;        // 207 KB of shared memory at r = 384
+constexpr int kWThreads = 128;
+constexpr int kWRows = kWThreads / 2;   // 4 rows per thread, 8 threads per row group
+constexpr int kWLd = kWRows + 4;        // column stride of the row block (16-byte aligned)
+constexpr int kTLd = PB + 4;            // row stride of a staged 32 x 32 tile
+constexpr int kWMaxR = 384;             // 113 KB of shared memory at r = 384: two CTAs per SM
+constexpr int kWPer = PB * PB / kWThreads;   // tile elements staged per thread
+constexpr int kWF4 = kWRows / 4;             // float4s per column of the row block
 
 size_t trsm_wide_smem(int r) { return (size_t)(r * kWLd + 2 * PB * kTLd) * sizeof(float); }
 
-__global__ void __launch_bounds__(kTrsm, 1)
+__global__ void __launch_bounds__(kWThreads, 2)
 trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __restrict__ L,
                  const float* __restrict__ dinv, const float* __restrict__ Linv_blk, float* __restrict__ V, int round,
                  const int* __restrict__ skip) {
@@ -1173,28 +1177,28 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
   const int64_t row0 = (int64_t)blockIdx.x * kWRows;
   if ((s & 3) == 0 && row0 + kWRows <= s && (reinterpret_cast<uintptr_t>(W) & 15) == 0) {
     // whole row block, 16-byte aligned: float4 loads of 4 consecutive rows,
-    // eight in flight per thread (a warp reads one 512-byte column run)
-    const int n4 = r * (kWRows / 4);
-    for (int e0 = t; e0 < n4; e0 += 8 * kTrsm) {
+    // eight in flight per thread (consecutive lanes read one column run)
+    const int n4 = r * kWF4;
+    for (int e0 = t; e0 < n4; e0 += 8 * kWThreads) {
       float4 v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kTrsm;
-        if (e < n4) v[u] = __ldg(reinterpret_cast<const float4*>(W + row0 + s * (e >> 5)) + (e & 31));
+        const int e = e0 + u * kWThreads;
+        if (e < n4) v[u] = __ldg(reinterpret_cast<const float4*>(W + row0 + s * (e / kWF4)) + (e % kWF4));
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * kTrsm;
+        const int e = e0 + u * kWThreads;
         if (e < n4) {
-          const int c = e >> 5;
+          const int c = e / kWF4;
           const float d = dinv[c];
-          *reinterpret_cast<float4*>(Vt + c * kWLd + 4 * (e & 31)) =
+          *reinterpret_cast<float4*>(Vt + c * kWLd + 4 * (e % kWF4)) =
               make_float4(v[u].x * d, v[u].y * d, v[u].z * d, v[u].w * d);
         }
       }
     }
   } else {
-    for (int e = t; e < kWRows * r; e += kTrsm) {
+    for (int e = t; e < kWRows * r; e += kWThreads) {
       const int ii = e % kWRows, c = e / kWRows;
       const int64_t row = row0 + ii;
       Vt[c * kWLd + ii] = (row < s) ? W[row + s * c] * dinv[c] : 0.f;
@@ -1208,10 +1212,10 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
   // for j < cb, then (L_bb)^-1, all in one stream of tiles.
   const int nb = (r + PB - 1) / PB;
   // tile q of the stream: (block, j); j == block means the inverted diagonal block
-  auto tile_load = [&](int cbq, int j, float (&pre)[4]) {
+  auto tile_load = [&](int cbq, int j, float (&pre)[kWPer]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = t + q * kTrsm;
+    for (int q = 0; q < kWPer; ++q) {
+      const int e = t + q * kWThreads;
       if (j < cbq) {   // Lk[k][c] = L[c0 + c][32 j + k]
         const int c = e & 31, k = e >> 5;
         pre[q] = (PB * cbq + c < r) ? L[(PB * cbq + c) + (int64_t)r * (PB * j + k)] : 0.f;
@@ -1221,15 +1225,15 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
       }
     }
   };
-  auto tile_store = [&](float* buf, int cbq, int j, const float (&pre)[4]) {
+  auto tile_store = [&](float* buf, int cbq, int j, const float (&pre)[kWPer]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = t + q * kTrsm;
+    for (int q = 0; q < kWPer; ++q) {
+      const int e = t + q * kWThreads;
       if (j < cbq) buf[(e >> 5) * kTLd + (e & 31)] = pre[q];
       else buf[(e & 31) * kTLd + (e >> 5)] = pre[q];
     }
   };
-  float pre[4];
+  float pre[kWPer];
   int cbn = 0, jn = 0;   // next tile to load
   tile_load(cbn, jn, pre);
   int bsel = 0;
@@ -1299,14 +1303,14 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
   }
   __syncthreads();
   if ((s & 3) == 0 && row0 + kWRows <= s && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
-    for (int e = t; e < r * (kWRows / 4); e += kTrsm) {
-      const int c = e >> 5;
-      float4 v = *reinterpret_cast<const float4*>(Vt + c * kWLd + 4 * (e & 31));
+    for (int e = t; e < r * kWF4; e += kWThreads) {
+      const int c = e / kWF4;
+      float4 v = *reinterpret_cast<const float4*>(Vt + c * kWLd + 4 * (e % kWF4));
       if (round) v = make_float4(mes::round_tf32(v.x), mes::round_tf32(v.y), mes::round_tf32(v.z), mes::round_tf32(v.w));
-      reinterpret_cast<float4*>(V + row0 + s * c)[e & 31] = v;
+      reinterpret_cast<float4*>(V + row0 + s * c)[e % kWF4] = v;
     }
   } else {
-    for (int e = t; e < kWRows * r; e += kTrsm) {
+    for (int e = t; e < kWRows * r; e += kWThreads) {
       const int ii = e % kWRows, c = e / kWRows;
       const int64_t row = row0 + ii;
       if (row < s) {
@@ -1354,7 +1358,7 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
       wattr = true;
     }
     const unsigned grid = (unsigned)((s + kWRows - 1) / kWRows);
-    trsm_wide_kernel<<<grid, kTrsm, trsm_wide_smem(r), st>>>(W, s, r, L, dinv, Linv_blk, V, round ? 1 : 0, skip);
+    trsm_wide_kernel<<<grid, kWThreads, trsm_wide_smem(r), st>>>(W, s, r, L, dinv, Linv_blk, V, round ? 1 : 0, skip);
     MES_LAUNCH_CHECK();
     return MES_OK;
   }
