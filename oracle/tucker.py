@@ -12,6 +12,9 @@ element-wise Eq. 2).
   T x_1 S^(1)T ... x_N S^(N)T (Eq. 5 and Eq. 7).  The singular vectors are
   taken as eigenvectors of the unfolding's Gram, as the paper does for the
   sweeps (text after Eq. 8).
+* Interlaced initialisation (st_hosvd): the paper's cheaper alternative to
+  T-HOSVD; mode n's factor comes from the tensor already truncated in modes
+  1..n-1.  Pinned by the exact error identity of sequential projections.
 * Sweep: for n = 1..N in order, Y^(n) = T x_{i != n} S^(i)T (Eq. 8), and
   S^(n) = the R_n leading left singular vectors of Y^(n)_(n), computed as the
   leading eigenvectors of the Gram Y^(n)_(n) Y^(n)_(n)^T.
@@ -99,6 +102,26 @@ def thosvd(T: np.ndarray, ranks):
         U, _ = leading_eigvecs(gram(Tn), r)
         factors.append(U)
     return factors
+
+
+def st_hosvd(T: np.ndarray, ranks):
+    """Interlaced (sequentially truncated) HOSVD, which the paper offers as
+    the cheaper way to the initial factors (end of the initialisation
+    subsection, after Eq. 7).  Modes are taken in the order 1..N; each mode's
+    factor holds the leading r_n eigenvectors of the Gram of the tensor
+    already truncated in the earlier modes, and the tensor is then truncated
+    in that mode:  S^(n) from G_(n) G_(n)^T,  G <- G x_n S^(n)T.
+    Returns the factors and, per mode, the energy that step drops (trace of
+    the Gram minus its kept eigenvalues)."""
+    G = np.asarray(T, dtype=np.float64)
+    factors, dropped = [], []
+    for n, r in enumerate(ranks):
+        Gn = gram(unfold(G, n))
+        U, lead = leading_eigvecs(Gn, r)
+        factors.append(U)
+        dropped.append(float(np.trace(Gn) - np.sum(lead)))
+        G = mode_product(G, U.T, n)
+    return factors, dropped
 
 
 @dataclasses.dataclass

@@ -213,3 +213,45 @@ def test_element_wise_model_matches_reconstruction():
             want += term
         assert abs(tucker.element(core, Us, idx) - want) < 1e-12
         assert abs(full[idx] - want) < 1e-12
+
+
+def test_st_hosvd_error_is_the_sum_of_dropped_eigenvalues():
+    # The truncations of ST-HOSVD are orthogonal projections applied one
+    # after another, so ||T - T_hat||^2 splits exactly into the energy each
+    # step drops: the sum over modes of the discarded eigenvalues of the Gram
+    # of the tensor truncated so far (an identity, not a bound).
+    rng = np.random.default_rng(31)
+    T = rng.standard_normal((9, 7, 5, 4))
+    ranks = (4, 3, 2, 3)
+    Us, dropped = tucker.st_hosvd(T, ranks)
+    Xh = tucker.reconstruct(tucker.core_of(T, Us), Us)
+    err2 = np.sum((T - Xh) ** 2)
+    assert abs(err2 - sum(dropped)) < 1e-10 * np.sum(T ** 2)
+    for U in Us:
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13
+
+
+def test_st_hosvd_order2_is_truncated_svd():
+    # For a matrix, truncating the rows first leaves U1^T T, whose leading
+    # right singular vectors are those of T: the result is the Eckart-Young
+    # truncated SVD (same fit as numpy's SVD)
+    rng = np.random.default_rng(32)
+    T = rng.standard_normal((12, 9))
+    Us, _ = tucker.st_hosvd(T, (4, 4))
+    Xh = tucker.reconstruct(tucker.core_of(T, Us), Us)
+    sv = np.linalg.svd(T, compute_uv=False)
+    assert abs(np.sum((T - Xh) ** 2) - np.sum(sv[4:] ** 2)) < 1e-10 * np.sum(T ** 2)
+
+
+def test_st_hosvd_full_rank_is_exact_and_hooi_reaches_the_same_fit():
+    rng = np.random.default_rng(33)
+    T = rng.standard_normal((6, 5, 3, 2))
+    Us, dropped = tucker.st_hosvd(T, T.shape)
+    assert max(dropped) < 1e-10
+    assert tucker.relative_error(T, tucker.reconstruct(tucker.core_of(T, Us), Us)) < 1e-13
+    # started from either initialisation, HOOI converges to the same fit here
+    T2 = rng.standard_normal((10, 8, 3, 2))
+    ranks = (4, 3, 3, 2)
+    a = tucker.hooi(T2, ranks, 200, 1e-14)
+    b = tucker.hooi(T2, ranks, 200, 1e-14, init_factors=tucker.st_hosvd(T2, ranks)[0])
+    assert abs(a.fit - b.fit) < 1e-9
