@@ -64,6 +64,16 @@ typedef enum mes_precision {
   MES_PREC_TF32 = 2   /* tensor-core TF32 inputs (FP32 data), FP32 accum.  */
 } mes_precision;
 
+typedef enum mes_init {
+  MES_INIT_THOSVD = 0,      /* truncated HOSVD (Eq. 6, Eq. 7): every factor
+                               from the unfolding Gram of T itself          */
+  MES_INIT_INTERLACED = 1   /* interlaced HOSVD (end of the initialisation
+                               subsection): modes in order 1..N, mode n's
+                               factor from the Gram of T already truncated
+                               in modes 1..n-1 (T x_1 S^(1)T ...), so the
+                               later modes work on a smaller tensor         */
+} mes_init;
+
 /* Thread-local text of the last error on this thread ("" if none). */
 const char* mes_last_error(void);
 
@@ -111,6 +121,8 @@ typedef struct mes_als_opts {
   int canonical;        /* 0 = default (1): rotate each factor to the
                            eigenvectors of the core's mode-n Gram, sorted by
                            decreasing eigenvalue, sign-fixed; -1 = off        */
+  int init;             /* mes_init of the start when init_factors is null
+                           (MES_INIT_THOSVD)                                  */
 } mes_als_opts;
 
 /*
@@ -118,7 +130,7 @@ typedef struct mes_als_opts {
  *
  * Computes T ~= Q x_1 S^(1) x_2 ... x_N S^(N) (Eq. 1) with orthonormal
  * factors S^(n) (s_n x r_n), initialised by the truncated HOSVD (Eq. 6,
- * Eq. 7) and refined by sweeps n = 1..N in which S^(n) becomes the r_n
+ * Eq. 7) or the interlaced HOSVD (opts->init) and refined by sweeps n = 1..N in which S^(n) becomes the r_n
  * leading left singular vectors of Y^(n) = T x_{i!=n} S^(i)T (Eq. 8), i.e.
  * the leading eigenvectors of the Gram Y^(n)_(n) Y^(n)_(n)^T.
  *

@@ -24,6 +24,7 @@ __all__ = ["colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequ
 MesError = _lib.MesError
 PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2}
 SPACES = {"ycbcr": 0, "ipt": 1}
+INITS = {"thosvd": 0, "interlaced": 1}
 
 
 def _torch():
@@ -85,12 +86,15 @@ def colour_convert(rgb8, space: str = "ycbcr", gamma: float = 2.2, out=None, nor
 
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
                precision: str = "fp32", init_iters: int = 0, inner_iters: int = 0, seed: int = 0,
-               canonical: bool = True, init_factors=None, history: bool = False, outputs=None):
+               canonical: bool = True, init_factors=None, history: bool = False, outputs=None,
+               init: str = "thosvd"):
     """Tucker-ALS / HOOI (Section III-B).  X: float32 CUDA tensor holding the
     first-mode-fastest tensor of paper dims `dims`.  Returns a dict with
     `core` (torch shape reversed(ranks)), `factors` (list of (r_n, s_n)
     tensors = column-major S^(n)), `fit` (float64 CUDA scalar), `iters`
-    (int32 CUDA scalar) and, if history, `fit_history` (max_iters float64)."""
+    (int32 CUDA scalar) and, if history, `fit_history` (max_iters float64).
+    init: "thosvd" (truncated HOSVD) or "interlaced" (interlaced HOSVD); a
+    given `init_factors` overrides both."""
     torch = _torch()
     _need(X, torch.float32, "X")
     dims = [int(d) for d in dims]
@@ -119,6 +123,7 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     opts.inner_iters = int(inner_iters)
     opts.seed = int(seed)
     opts.canonical = 0 if canonical else -1
+    opts.init = INITS[init]
     opts.iters_done = iters.data_ptr()
     opts.fit_history = hist.data_ptr() if hist is not None else None
     keep = None

@@ -69,6 +69,7 @@ class MesAlsOpts(ctypes.Structure):
         ("iters_done", ctypes.c_void_p),
         ("fit_history", ctypes.c_void_p),
         ("canonical", ctypes.c_int),
+        ("init", ctypes.c_int),
     ]
 
 

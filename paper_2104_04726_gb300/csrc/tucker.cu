@@ -397,6 +397,8 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   const bool canonical = o.canonical >= 0;
   if (o.init_iters < 0 || o.inner_iters < 0)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: negative iteration option");
+  if (o.init != MES_INIT_THOSVD && o.init != MES_INIT_INTERLACED)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: unknown init %d", o.init);
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
@@ -508,85 +510,14 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   const float* Xop = tf32 ? Xr : X;    // T as an operand of the large products
   MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
 
-  // ---- initialisation: truncated HOSVD (Eq. 6, Eq. 7) or given factors ----
-  if (o.init_factors) {
-    for (int n = 0; n < N; ++n) {
-      if (!o.init_factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: init_factors[%d] null", n);
-      MES_CUDA_TRY(cudaMemcpyAsync(factors[n], o.init_factors[n], sizeof(float) * sh.s[n] * sh.r[n],
-                                   cudaMemcpyDeviceToDevice, st));
-      if (tf32 && n < 2) MES_TRY(mes::round_copy(factors[n], Ur[n], sh.s[n] * sh.r[n], nullptr, st));
-      if (bf && n < 2) MES_TRY(mes::to_bf16(factors[n], U16[n], sh.s[n] * sh.r[n], nullptr, st));
-    }
-  } else {
-    // small modes: exact eigenvectors of the unfolding Grams of T.  A small
-    // mode at full rank has an orthogonal factor: it changes neither the
-    // other modes' Grams nor the core norm, and its eigenvectors are taken
-    // from the last sweep's B, so until then it starts as the identity.
-    for (int n = 2; n < N; ++n) {
-      if (sh.r[n] == sh.s[n]) {
-        MES_TRY(mes::identity_fill(factors[n], sh.s[n], (int)sh.r[n], st));
-        continue;
-      }
-      KronDesc kd;
-      kd.nm = sh.nsm;
-      for (int m = 0; m < sh.nsm; ++m) {
-        kd.s[m] = (int)sh.s[m + 2];
-        kd.r[m] = (int)sh.r[m + 2];
-        kd.op[m] = 'I';
-        kd.U[m] = nullptr;
-      }
-      Fibres fb;
-      fb.F_lo = s1 * s2; fb.F_hi = 1;
-      fb.in = X; fb.in_lo = 1; fb.in_hi = 0; fb.in_l = s1 * s2;
-      MES_TRY(d.small_update(fb, kd, n - 2, factors[n]));
-    }
-    // mode 1: T_(1) = rows x, columns (y, l); mode 2: rows y, columns (x, l)
-    for (int n = 0; n < 2; ++n) {
-      const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
-      float* S = factors[n];
-      MES_TRY(mes::uniform_fill(d.W, s * r, seed * 2 + n, st));
-      MES_TRY(d.orth(d.W, s, r, S, Ur[n], true));
-      if (bf) MES_TRY(mes::to_bf16(S, U16[n], s * r, nullptr, st));
-      Gemm gz = base(), gw = base();
-      int64_t J;
-      if (n == 0) {
-        J = s2 * L;   // Z[(y,l)][q] = sum_x T[x + s1*(y,l)] S[x,q]
-        gz.M = J; gz.N = r; gz.K_lo = s1;
-        gz.A = Xop; gz.a_m = s1; gz.a_k = 1;
-        // W[x][q] = sum_{y,l} XB[y + s2*x + s1*s2*l] Zh[(y + s2*l) + J*q]
-        gw.M = s1; gw.N = r; gw.K_lo = s2; gw.K_hi = L;
-        gw.A = XB; gw.a_m = s2; gw.a_k = 1; gw.a_kh = s1 * s2;
-        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s2;
-      } else {
-        J = s1 * L;   // Z[(x,l)][q] = sum_y XB[y + s2*(x + s1*l)] S[y,q]
-        gz.M = J; gz.N = r; gz.K_lo = s2;
-        gz.A = XB; gz.a_m = s2; gz.a_k = 1;
-        // W[y][q] = sum_{x,l} X[x + s1*y + s1*s2*l] Zh[(x + s1*l) + J*q]
-        gw.M = s2; gw.N = r; gw.K_lo = s1; gw.K_hi = L;
-        gw.A = Xop; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
-        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s1;
-      }
-      // BF16 form: the same products on the BF16 copies of T
-      Gemm gz16 = gz, gw16 = gw;
-      if (bf) {
-        gz16.A = reinterpret_cast<const float*>(n == 0 ? X16 : XB16);
-        gw16.A = reinterpret_cast<const float*>(n == 0 ? XB16 : X16);
-      }
-      for (int it = 0; it < init_iters; ++it)
-        MES_TRY(d.subspace_step(gz, gw, J, s, r, S, Ur[n], true, bf ? &gz16 : nullptr, bf ? &gw16 : nullptr,
-                                bf ? U16[n] : nullptr));
-    }
-  }
-
-  // ---- sweeps (Eq. 8), n = 1..N ----
-  d.skip = done;
-  // factor of small mode n from the Gram of B x_{m != n, m >= 3} S_m^T
-  auto small_mode_update = [&](int n) -> mes_status {
+  // factor of small mode n from the Gram of B x_{m != n, m >= 3} S_m^T; in
+  // the interlaced initialisation only the modes before n are truncated
+  auto small_mode_update = [&](int n, bool interlaced) -> mes_status {
     KronDesc kd;
     kd.nm = sh.nsm;
     for (int m = 0; m < sh.nsm; ++m) {
       kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2];
-      kd.op[m] = (m + 2 == n) ? 'I' : 'T';
+      kd.op[m] = (m + 2 == n || (interlaced && m + 2 > n)) ? 'I' : 'T';
       kd.U[m] = factors[m + 2];
     }
     Fibres fb;
@@ -652,6 +583,107 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     g.C = Bt; g.c_m = 1; g.c_n = r1 * L;
     return d.big(g);
   };
+  // ---- initialisation: truncated or interlaced HOSVD (Eq. 6, Eq. 7) or given factors ----
+  if (o.init_factors) {
+    for (int n = 0; n < N; ++n) {
+      if (!o.init_factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: init_factors[%d] null", n);
+      MES_CUDA_TRY(cudaMemcpyAsync(factors[n], o.init_factors[n], sizeof(float) * sh.s[n] * sh.r[n],
+                                   cudaMemcpyDeviceToDevice, st));
+      if (tf32 && n < 2) MES_TRY(mes::round_copy(factors[n], Ur[n], sh.s[n] * sh.r[n], nullptr, st));
+      if (bf && n < 2) MES_TRY(mes::to_bf16(factors[n], U16[n], sh.s[n] * sh.r[n], nullptr, st));
+    }
+  } else {
+    const bool interlaced = o.init == MES_INIT_INTERLACED;
+    // small modes: exact eigenvectors of the unfolding Grams of T (of the
+    // truncated tensor, below, in the interlaced form).  A small mode at
+    // full rank has an orthogonal factor: it changes neither the other
+    // modes' Grams nor the core norm, and its eigenvectors are taken from
+    // the last sweep's B, so until then it starts as the identity.
+    for (int n = 2; n < N; ++n) {
+      if (sh.r[n] == sh.s[n]) {
+        MES_TRY(mes::identity_fill(factors[n], sh.s[n], (int)sh.r[n], st));
+        continue;
+      }
+      if (interlaced) continue;
+      KronDesc kd;
+      kd.nm = sh.nsm;
+      for (int m = 0; m < sh.nsm; ++m) {
+        kd.s[m] = (int)sh.s[m + 2];
+        kd.r[m] = (int)sh.r[m + 2];
+        kd.op[m] = 'I';
+        kd.U[m] = nullptr;
+      }
+      Fibres fb;
+      fb.F_lo = s1 * s2; fb.F_hi = 1;
+      fb.in = X; fb.in_lo = 1; fb.in_hi = 0; fb.in_l = s1 * s2;
+      MES_TRY(d.small_update(fb, kd, n - 2, factors[n]));
+    }
+    // mode 1: T_(1) = rows x, columns (y, l); mode 2: rows y, columns (x, l)
+    // (the interlaced form takes only mode 1 from T itself)
+    for (int n = 0; n < (interlaced ? 1 : 2); ++n) {
+      const int64_t s = n == 0 ? s1 : s2, r = n == 0 ? r1 : r2;
+      float* S = factors[n];
+      MES_TRY(mes::uniform_fill(d.W, s * r, seed * 2 + n, st));
+      MES_TRY(d.orth(d.W, s, r, S, Ur[n], true));
+      if (bf) MES_TRY(mes::to_bf16(S, U16[n], s * r, nullptr, st));
+      Gemm gz = base(), gw = base();
+      int64_t J;
+      if (n == 0) {
+        J = s2 * L;   // Z[(y,l)][q] = sum_x T[x + s1*(y,l)] S[x,q]
+        gz.M = J; gz.N = r; gz.K_lo = s1;
+        gz.A = Xop; gz.a_m = s1; gz.a_k = 1;
+        // W[x][q] = sum_{y,l} XB[y + s2*x + s1*s2*l] Zh[(y + s2*l) + J*q]
+        gw.M = s1; gw.N = r; gw.K_lo = s2; gw.K_hi = L;
+        gw.A = XB; gw.a_m = s2; gw.a_k = 1; gw.a_kh = s1 * s2;
+        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s2;
+      } else {
+        J = s1 * L;   // Z[(x,l)][q] = sum_y XB[y + s2*(x + s1*l)] S[y,q]
+        gz.M = J; gz.N = r; gz.K_lo = s2;
+        gz.A = XB; gz.a_m = s2; gz.a_k = 1;
+        // W[y][q] = sum_{x,l} X[x + s1*y + s1*s2*l] Zh[(x + s1*l) + J*q]
+        gw.M = s2; gw.N = r; gw.K_lo = s1; gw.K_hi = L;
+        gw.A = Xop; gw.a_m = s1; gw.a_k = 1; gw.a_kh = s1 * s2;
+        gw.B = d.Zh; gw.b_n = J; gw.b_k = 1; gw.b_kh = s1;
+      }
+      // BF16 form: the same products on the BF16 copies of T
+      Gemm gz16 = gz, gw16 = gw;
+      if (bf) {
+        gz16.A = reinterpret_cast<const float*>(n == 0 ? X16 : XB16);
+        gw16.A = reinterpret_cast<const float*>(n == 0 ? XB16 : X16);
+      }
+      for (int it = 0; it < init_iters; ++it)
+        MES_TRY(d.subspace_step(gz, gw, J, s, r, S, Ur[n], true, bf ? &gz16 : nullptr, bf ? &gw16 : nullptr,
+                                bf ? U16[n] : nullptr));
+    }
+    if (interlaced) {
+      // mode 2 from the tensor truncated in mode 1, Ca = T x_1 S1^T (rows y,
+      // J = r1 L columns instead of s1 L):
+      //   Z[j][q] = sum_y Cat[y + s2 j] S[y][q],  W[y][q] = sum_j Ca[j + J y] Zh[j + J q]
+      MES_TRY(ca_product(bf));
+      const int64_t J = r1 * L;
+      MES_TRY(mes::uniform_fill(d.W, s2 * r2, seed * 2 + 1, st));
+      MES_TRY(d.orth(d.W, s2, r2, U1, Ur[1], true));
+      if (bf) MES_TRY(mes::to_bf16(U1, U16[1], s2 * r2, nullptr, st));
+      Gemm gz = base(), gw = base();
+      gz.M = J; gz.N = r2; gz.K_lo = s2;
+      gz.A = Cat; gz.a_m = s2; gz.a_k = 1;
+      gw.M = s2; gw.N = r2; gw.K_lo = J;
+      gw.A = Ca; gw.a_m = J; gw.a_k = 1;
+      gw.B = d.Zh; gw.b_n = J; gw.b_k = 1;
+      for (int it = 0; it < init_iters; ++it)
+        MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1, Ur[1], true, nullptr, nullptr, bf ? U16[1] : nullptr));
+      // small modes n = 3..N in order, each from B = Ca x_2 S2^T truncated in
+      // the small modes before n
+      if (!sh.small_full) {
+        MES_TRY(b_product());
+        for (int n = 2; n < N; ++n)
+          if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n, true));
+      }
+    }
+  }
+
+  // ---- sweeps (Eq. 8), n = 1..N ----
+  d.skip = done;
   for (int sweep = 1; sweep <= max_iters; ++sweep) {
     // mode 1: P = T x_2 S2^T, per l: P[x][q2 + r2 l] = sum_y XB[y + s2 x + s1 s2 l] U1[y + s2 q2]
     {
@@ -737,7 +769,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     // every other mode's Gram and the core norm unchanged, so its
     // eigenvectors are taken once, after the last sweep.
     for (int n = 2; n < N; ++n)
-      if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n));
+      if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n, false));
     // core Q = B x_{n>=3} S_n^T (Eq. 5 / Eq. 7 with the current factors)
     {
       MES_TRY(core_from_B(done));
@@ -761,7 +793,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     bool any_full = false;
     for (int n = 2; n < N; ++n)
       if (sh.r[n] == sh.s[n]) {
-        MES_TRY(small_mode_update(n));
+        MES_TRY(small_mode_update(n, false));
         any_full = true;
       }
     if (any_full) MES_TRY(core_from_B(nullptr));

@@ -132,3 +132,20 @@ def test_workspace_size_query_without_gpu(lib):
     n = ctypes.c_size_t()
     assert lib.mes_tucker_als_workspace_size(4, _i64([8, 6, 3, 2]), _i64([9, 2, 1, 1]), None, ctypes.byref(n)) == 2
     assert lib.mes_tucker_als_workspace_size(4, _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1]), None, None) == 1
+
+
+def test_init_option_validated_without_gpu(lib):
+    from paper_2104_04726_gb300 import _lib
+    n = ctypes.c_size_t()
+    dims, ranks = _i64([8, 6, 3, 2]), _i64([2, 2, 1, 1])
+    for init, want in ((0, 0), (1, 0), (2, 1), (-1, 1)):
+        o = _lib.MesAlsOpts()
+        o.init = init
+        assert lib.mes_tucker_als_workspace_size(4, dims, ranks, ctypes.byref(o), ctypes.byref(n)) == want, init
+    # both starts use the same workspace
+    o0, o1 = _lib.MesAlsOpts(), _lib.MesAlsOpts()
+    o1.init = 1
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.mes_tucker_als_workspace_size(4, dims, ranks, ctypes.byref(o0), ctypes.byref(a))
+    lib.mes_tucker_als_workspace_size(4, dims, ranks, ctypes.byref(o1), ctypes.byref(b))
+    assert a.value == b.value

@@ -450,3 +450,56 @@ def test_precision_forms_against_oracle_xga(mes):
               f"rel err {rel:.6e} (oracle {1 - ref.fit:.6e}); PSNR {ps:.3f} dB (oracle {psnr_o:.3f})")
         assert abs(fit - ref.fit) / ref.fit < tol, prec
         assert abs(rel - (1 - ref.fit)) / (1 - ref.fit) < 0.05, prec
+
+
+def _two_block_tensor(seed):
+    """40 x 32 x 3 x 6 tensor built from two blocks of a Tucker core: rows 0..7
+    of mode 1 pair with columns 0..5 of mode 2, rows 8..31 with columns
+    6..11.  Truncating mode 1 first (the interlaced HOSVD) removes most of the
+    second block before mode 2 is chosen, so the two initialisations lead
+    HOOI to different local optima (fits about 10% apart)."""
+    rng = np.random.default_rng(seed)
+    C = np.zeros((32, 12, 3, 6))
+    C[:8, :6] = 1.5 * rng.standard_normal((8, 6, 3, 6))
+    C[8:, 6:] = 1.2 * rng.standard_normal((24, 6, 3, 6))
+    C *= np.array([1.0, 0.6, 0.35])[None, None, :, None]
+    C *= (0.8 ** np.arange(6))[None, None, None, :]
+    T = C
+    for n, (s, r) in enumerate(((40, 32), (32, 12), (3, 3), (6, 6))):
+        T = tucker.mode_product(T, np.linalg.qr(rng.standard_normal((s, r)))[0], n)
+    return T + 1e-4 * rng.standard_normal(T.shape)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 2e-3)])
+@pytest.mark.parametrize("ranks", [(8, 6, 3, 6), (8, 6, 2, 3)])
+def test_interlaced_init_follows_the_oracle(mes, ranks, prec, tol):
+    """The interlaced start (mode n's factor from T truncated in modes
+    1..n-1) against the oracle's st_hosvd: with the subspace iterations run
+    to convergence, the fit after one sweep and after ten matches HOOI
+    started from the oracle's interlaced factors, on a tensor where the
+    truncated-HOSVD start ends elsewhere."""
+    T = _two_block_tensor(7)
+    st_init = tucker.st_hosvd(T, ranks)[0]
+    for iters in (1, 10):
+        ref_st = tucker.hooi(T, ranks, iters, 0.0, init_factors=st_init)
+        ref_t = tucker.hooi(T, ranks, iters, 0.0)
+        assert abs(ref_st.fit - ref_t.fit) / ref_t.fit > 0.01      # the case discriminates
+        res = _run(mes, T, ranks, iters, 0.0, init="interlaced", init_iters=200, inner_iters=60,
+                   precision=prec)
+        fit = float(res["fit"].cpu())
+        print(f"{ranks} {prec} {iters} sweeps: fit {fit:.9f} oracle interlaced {ref_st.fit:.9f} "
+              f"truncated {ref_t.fit:.9f}")
+        assert abs(fit - ref_st.fit) / ref_st.fit < tol, (fit, ref_st.fit, ref_t.fit)
+        for U in factors_np(res):
+            assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 5e-6
+
+
+def test_interlaced_init_converges_to_the_scene_fit(mes):
+    """On the 64x48 scene both starts reach the oracle's converged fit."""
+    cfg, img = _scene("small_64x48")
+    T = colour.colour_convert(img, cfg["space"])
+    ref = tucker.hooi(T, cfg["ranks"], cfg["iters"], cfg["tol"])
+    for init in ("thosvd", "interlaced"):
+        res = _run(mes, T, cfg["ranks"], cfg["iters"], cfg["tol"], inner_iters=4, init=init)
+        fit = float(res["fit"].cpu())
+        assert abs(fit - ref.fit) / ref.fit < 1e-5, (init, fit, ref.fit)
