@@ -87,3 +87,83 @@ def test_stack_layout():
     for (x, y, k) in [(0, 0, 0), (6, 4, 3), (3, 2, 1)]:
         want = colour.ycbcr601(colour.rgb_prime(img[k, y, x]))
         np.testing.assert_allclose(T[x, y, :, k], want, atol=1e-15)
+
+
+# ---- constant-luminance BT.2020 Y'CbCr and the inverse transforms ----
+
+_D65 = (0.3127, 0.3290)
+_PRIM_709 = ((0.640, 0.330), (0.300, 0.600), (0.150, 0.060))
+_PRIM_2020 = ((0.708, 0.292), (0.170, 0.797), (0.131, 0.046))
+
+
+def _npm(prims, white):
+    """Normalised primary matrix (linear RGB -> XYZ) from the xy
+    chromaticities of the primaries and the white point: columns are the
+    primaries' XYZ scaled so that RGB = (1,1,1) gives the white with Y = 1."""
+    P = np.array([[x / y, 1.0, (1 - x - y) / y] for x, y in prims]).T
+    wx, wy = white
+    W = np.array([wx / wy, 1.0, (1 - wx - wy) / wy])
+    return P * np.linalg.solve(P, W)
+
+
+def test_bt2020_luminance_weights_from_the_primaries():
+    # the luminance row of the BT.2020 primary matrix, derived here from the
+    # chromaticities, equals the published weights (four digits)
+    np.testing.assert_allclose(_npm(_PRIM_2020, _D65)[1], [colour.KR20, colour.KG20, colour.KB20], atol=5e-5)
+    # and the same derivation gives the BT.601/709 weights' row for 709 primaries
+    np.testing.assert_allclose(_npm(_PRIM_709, _D65)[1], [0.2126, 0.7152, 0.0722], atol=5e-5)
+
+
+def test_709_to_2020_matrix_from_the_primaries():
+    M = np.linalg.solve(_npm(_PRIM_2020, _D65), _npm(_PRIM_709, _D65))
+    np.testing.assert_allclose(colour.M_709_TO_2020, M, atol=1e-4)
+    np.testing.assert_allclose(colour.M_709_TO_2020.sum(axis=1), 1.0, atol=1e-12)
+
+
+def test_bt2020_transfer_function():
+    assert colour.bt2020_oetf(0.0) == 0.0
+    assert abs(colour.bt2020_oetf(1.0) - 1.0) < 1e-12
+    b = colour.OETF_BETA
+    # the two segments meet at beta (to the four digits of the constants)
+    assert abs(4.5 * b - (colour.OETF_ALPHA * b ** 0.45 - (colour.OETF_ALPHA - 1))) < 2e-5
+    E = np.linspace(-0.05, 1.0, 2001)
+    Ep = colour.bt2020_oetf(E)
+    assert np.all(np.diff(Ep) > 0)
+    np.testing.assert_allclose(colour.bt2020_oetf_inverse(Ep), E, atol=1e-12)
+
+
+@pytest.mark.parametrize("rgb,chan,want", [((0, 0, 1), 1, 0.5), ((1, 1, 0), 1, -0.5),
+                                           ((1, 0, 0), 2, 0.5), ((0, 1, 1), 2, -0.5)])
+def test_cl_chroma_reaches_its_range_at_the_primaries(rgb, chan, want):
+    # BT.2020 sizes the four chroma divisors so that the BT.2020 primaries and
+    # secondaries land on +-1/2: blue and yellow on Cb, red and cyan on Cr.
+    # The branch (divisor by sign) is what puts each extreme on +-1/2.
+    ycc = colour.ycbcr2020cl_from_linear(np.array(rgb, dtype=np.float64))
+    assert abs(ycc[chan] - want) < 3e-4
+
+
+def test_cl_grey_axis():
+    v = np.arange(256, dtype=np.uint8)
+    g = v / 255.0
+    for gamma in (2.2, 1.0):
+        ycc = colour.ycbcr2020cl(colour.rgb_prime(np.stack([v, v, v], 1)), gamma)
+        np.testing.assert_allclose(ycc[:, 0], colour.bt2020_oetf(g ** gamma), atol=1e-12)
+        assert np.abs(ycc[:, 1:]).max() < 1e-12
+
+
+@pytest.mark.parametrize("space", ["ycbcr", "ipt", "ycbcr2020cl"])
+def test_inverse_transforms_recover_the_images(space):
+    rng = np.random.default_rng(11)
+    rgb8 = rng.integers(0, 256, size=(3, 7, 9, 3), dtype=np.uint8)
+    rgb8[0, 0, :4] = [[0, 0, 0], [255, 255, 255], [255, 0, 0], [0, 0, 255]]
+    T = colour.colour_convert(rgb8, space)
+    back = colour.colour_invert(T, space)
+    # FP64 round-off near black is raised to the power 1/gamma: 1e-6, far
+    # inside the half step 0.5/255 that the 8-bit recovery needs
+    np.testing.assert_allclose(back, colour.rgb_prime(rgb8), atol=1e-6)
+    assert np.array_equal(colour.to_u8(back), rgb8)
+
+
+def test_to_u8_rounds_half_to_even_and_clamps():
+    x = np.array([-0.1, 0.0, 0.5 / 255, 1.5 / 255, 2.5 / 255, 254.5 / 255, 1.0, 1.2])
+    assert colour.to_u8(x).tolist() == [0, 0, 0, 2, 2, 254, 255, 255]
