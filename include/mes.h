@@ -50,7 +50,14 @@ typedef enum mes_status {
 
 typedef enum mes_colour {
   MES_YCBCR601 = 0,   /* ITU-R BT.601 Y'CbCr, full range, no offsets        */
-  MES_IPT = 1         /* Ebner-Fairchild IPT from gamma-linearised sRGB    */
+  MES_IPT = 1,        /* Ebner-Fairchild IPT from gamma-linearised sRGB    */
+  MES_YCBCR2020CL = 2 /* ITU-R BT.2020 constant-luminance Y'CbCr from
+                         gamma-linearised sRGB: BT.709 -> BT.2020 primaries
+                         (BT.2087), Yc = 0.2627R + 0.6780G + 0.0593B,
+                         BT.2020 transfer function (alpha 1.0993, beta
+                         0.0181) on Yc, B, R; Cb, Cr divided by 1.9404 /
+                         1.5816 and 1.7184 / 0.9936 by the sign of the
+                         difference                                         */
 } mes_colour;
 
 typedef enum mes_precision {
@@ -88,8 +95,8 @@ const char* mes_version(void);
  *               interleaved R,G,B bytes: byte (k, y, x, c) at
  *               ((k*s2 + y)*s1 + x)*3 + c.  Image k = view*E + exposure.
  *  s1, s2, K    image width, height and count (each >= 1).
- *  space        MES_YCBCR601 or MES_IPT.
- *  gamma        IPT only: linearisation exponent R = (R')^gamma (> 0).
+ *  space        MES_YCBCR601, MES_IPT or MES_YCBCR2020CL.
+ *  gamma        IPT and BT.2020 CL: linearisation exponent R = (R')^gamma (> 0).
  *  out    [out] FP32 tensor of dims (s1, s2, 3, K), first mode fastest, i.e.
  *               channel plane (c, k) is the contiguous s1*s2 block number
  *               c + 3k.
@@ -101,6 +108,28 @@ const char* mes_version(void);
 mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K,
                               int space, float gamma, float* out, double* norm2,
                               void* stream);
+
+/*
+ * mes_colour_invert -- inverse of the colour pre-pass: a tensor in the colour
+ * space of Section III-A (typically the low-rank approximation from
+ * mes_reconstruct) back to 8-bit R'G'B' images, the form in which the
+ * approximated views go on to the 3D-HEVC encoder (Section III-C).  Each
+ * space is solved back to R'G'B' from its definition (mes_colour_convert);
+ * linear values below zero keep their sign through the power functions.
+ *
+ *  X      [in]  FP32 tensor of dims (s1, s2, 3, K), first mode fastest (the
+ *               layout mes_colour_convert writes).
+ *  s1, s2, K, space, gamma   as for mes_colour_convert.
+ *  rgb8   [out] nullable; K images in the layout mes_colour_convert reads,
+ *               each channel clamp(rint(255 R'), 0, 255), ties to even.
+ *  rgbp   [out] nullable; the same images as FP32 R'G'B' before rounding and
+ *               clamping (interleaved like rgb8).
+ * Errors: MES_ERR_INVALID_ARG for a null X, both outputs null, non-positive
+ *         sizes, an unknown space or gamma <= 0; MES_ERR_CUDA on a launch
+ *         failure.  A NaN gives byte 0, not an error.
+ */
+mes_status mes_colour_invert(const float* X, int64_t s1, int64_t s2, int64_t K, int space,
+                             float gamma, uint8_t* rgb8, float* rgbp, void* stream);
 
 /*
  * Options of mes_tucker_als.  Zero-initialise and set what you need; a NULL

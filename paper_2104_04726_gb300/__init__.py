@@ -18,12 +18,12 @@ from typing import Sequence
 
 from . import _lib
 
-__all__ = ["colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequantize_core",
+__all__ = ["colour_invert", "colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequantize_core",
            "version", "torch_shape", "paper_dims", "PRECISIONS", "SPACES", "MesError"]
 
 MesError = _lib.MesError
 PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2}
-SPACES = {"ycbcr": 0, "ipt": 1}
+SPACES = {"ycbcr": 0, "ipt": 1, "ycbcr2020cl": 2}
 INITS = {"thosvd": 0, "interlaced": 1}
 
 
@@ -82,6 +82,28 @@ def colour_convert(rgb8, space: str = "ycbcr", gamma: float = 2.2, out=None, nor
                                 _ptr(out), _ptr(norm2), _stream())
     _lib.check(st, "mes_colour_convert")
     return out, norm2
+
+
+def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=None, want_u8: bool = True,
+                  want_float: bool = False):
+    """Inverse colour transform: float32 CUDA tensor of torch shape
+    (K, 3, s2, s1) (paper dims (s1, s2, 3, K)) -> images (K, s2, s1, 3):
+    uint8 (clamp(rint(255 R'))) and/or float32 R'G'B'.  Returns (rgb8, rgbp),
+    None for an output not asked for."""
+    torch = _torch()
+    _need(X, torch.float32, "X")
+    K, c, s2, s1 = X.shape
+    if c != 3:
+        raise ValueError("X must have 3 channels")
+    if want_u8 and rgb8 is None:
+        rgb8 = torch.empty((K, s2, s1, 3), dtype=torch.uint8, device=X.device)
+    if want_float and rgbp is None:
+        rgbp = torch.empty((K, s2, s1, 3), dtype=torch.float32, device=X.device)
+    lib = _lib.load()
+    st = lib.mes_colour_invert(_ptr(X), s1, s2, K, SPACES[space], ctypes.c_float(gamma), _ptr(rgb8),
+                               _ptr(rgbp), _stream())
+    _lib.check(st, "mes_colour_invert")
+    return rgb8, rgbp
 
 
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,

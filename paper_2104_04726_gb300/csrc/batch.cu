@@ -31,7 +31,7 @@ mes_status problem_check(const mes_problem& p, size_t* ws_bytes) {
   if (p.rgb8) {
     if (p.N != 4 || p.dims[2] != 3)
       return mes::fail(MES_ERR_INVALID_ARG, "problem: 8-bit input needs dims (s1, s2, 3, K)");
-    if (p.space != MES_YCBCR601 && p.space != MES_IPT)
+    if (p.space != MES_YCBCR601 && p.space != MES_IPT && p.space != MES_YCBCR2020CL)
       return mes::fail(MES_ERR_INVALID_ARG, "problem: unknown colour space %d", p.space);
     if (p.gamma < 0.f) return mes::fail(MES_ERR_INVALID_ARG, "problem: gamma must be >= 0");
   }

@@ -1,11 +1,14 @@
-// Colour pre-pass (Section III-A): 8-bit R'G'B' images -> Y'CbCr (BT.601)
-// or IPT planes of the stacked tensor (Section III-B), with ||T||_F^2 fused.
+// Colour pre-pass (Section III-A): 8-bit R'G'B' images -> Y'CbCr (BT.601),
+// IPT or constant-luminance Y'CbCr (BT.2020) planes of the stacked tensor
+// (Section III-B), with ||T||_F^2 fused; and its inverse, tensor -> 8-bit
+// images (the approximated views handed to the encoder, Section III-C).
 //
 // Bandwidth kernel: each thread converts 8 consecutive pixels of one image
 // (24 bytes in, 96 bytes out as three float4 pairs, one per channel plane).
-// The u8 -> [0,1] scaling and the IPT linearisation go through a 256-entry
-// table built per block, so the only transcendental left per pixel is the
-// 0.43 power of the three cone responses.  The squared norm is accumulated
+// The u8 -> [0,1] scaling and the linearisation go through a 256-entry
+// table built per block, so the only transcendentals left per pixel are the
+// 0.43 power of the three cone responses (IPT) or the transfer function of
+// Yc, B and R (BT.2020 constant luminance).  The squared norm is accumulated
 // in FP64 per thread, reduced per block, and the per-block partials are
 // summed by one block in a fixed order, so the result is reproducible.
 #include "common.cuh"
@@ -13,11 +16,25 @@
 namespace {
 
 struct ColourParams {
-  float a[9];      // R,G,B (linear) -> L,M,S  (row-major 3x3)
-  float b[9];      // L',M',S' -> I,P,T       (row-major 3x3)
+  float a[9];      // IPT: R,G,B (linear) -> L,M,S; BT.2020 CL: BT.709 -> BT.2020 primaries
+  float b[9];      // IPT: L',M',S' -> I,P,T      (row-major 3x3)
   float gamma;
   int space;
 };
+
+// BT.2020 luminance weights, transfer function (12-bit constants) and the
+// constant-luminance chroma divisors N_b, P_b, N_r, P_r
+constexpr float kKr20 = 0.2627f, kKg20 = 0.6780f, kKb20 = 0.0593f;
+constexpr float kAlpha = 1.0993f, kBeta = 0.0181f;
+constexpr float kNb = 1.9404f, kPb = 1.5816f, kNr = 1.7184f, kPr = 0.9936f;
+
+__device__ __forceinline__ float oetf2020(float e) {
+  return e < kBeta ? 4.5f * e : fmaf(kAlpha, powf(e, 0.45f), -(kAlpha - 1.f));
+}
+
+__device__ __forceinline__ float oetf2020_inverse(float e) {
+  return e < 4.5f * kBeta ? e * (1.f / 4.5f) : powf((e + (kAlpha - 1.f)) / kAlpha, 1.f / 0.45f);
+}
 
 constexpr int kThreads = 256;
 constexpr int kPix = 8;
@@ -37,6 +54,16 @@ __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float
     c0 = y;
     c1 = (b - y) * (1.0f / 1.772f);
     c2 = (r - y) * (1.0f / 1.402f);
+  } else if (P.space == MES_YCBCR2020CL) {
+    float r = lut_lin[r8], g = lut_lin[g8], b = lut_lin[b8];
+    float R = fmaf(P.a[0], r, fmaf(P.a[1], g, P.a[2] * b));
+    float G = fmaf(P.a[3], r, fmaf(P.a[4], g, P.a[5] * b));
+    float B = fmaf(P.a[6], r, fmaf(P.a[7], g, P.a[8] * b));
+    float yc = oetf2020(fmaf(kKr20, R, fmaf(kKg20, G, kKb20 * B)));
+    float db = oetf2020(B) - yc, dr = oetf2020(R) - yc;
+    c0 = yc;
+    c1 = db <= 0.f ? db * (1.f / kNb) : db * (1.f / kPb);
+    c2 = dr <= 0.f ? dr * (1.f / kNr) : dr * (1.f / kPr);
   } else {
     float r = lut_lin[r8], g = lut_lin[g8], b = lut_lin[b8];
     float L = fmaf(P.a[0], r, fmaf(P.a[1], g, P.a[2] * b));
@@ -73,7 +100,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
   for (int v = threadIdx.x; v < 256; v += blockDim.x) {
     float p = (float)v / 255.0f;
     lut_p[v] = p;
-    lut_lin[v] = (P.space == MES_IPT) ? powf(p, P.gamma) : p;
+    lut_lin[v] = (P.space != MES_YCBCR601) ? powf(p, P.gamma) : p;
   }
   __syncthreads();
 
@@ -142,21 +169,160 @@ sum_partials_kernel(const double* __restrict__ partials, int n, double* __restri
   if (threadIdx.x == 0) *out = t;
 }
 
-void make_params(int space, float gamma, ColourParams* P) {
-  // Linear sRGB (D65) -> XYZ (IEC 61966-2-1) and XYZ -> LMS (Hunt-Pointer-
-  // Estevez normalised to D65), multiplied once here in double.
-  const double rgb2xyz[9] = {0.4124, 0.3576, 0.1805, 0.2126, 0.7152, 0.0722, 0.0193, 0.1192, 0.9505};
-  const double xyz2lms[9] = {0.4002, 0.7075, -0.0807, -0.2280, 1.1500, 0.0612, 0.0, 0.0, 0.9184};
-  const double lms2ipt[9] = {0.4000, 0.4000, 0.2000, 4.4550, -4.8510, 0.3960, 0.8056, 0.3572, -1.1628};
+// Linear sRGB (D65) -> XYZ (IEC 61966-2-1), XYZ -> LMS (Hunt-Pointer-Estevez
+// normalised to D65), L'M'S' -> IPT (Ebner-Fairchild), linear BT.709 ->
+// BT.2020 primaries (ITU-R BT.2087); row-major.
+const double kRgb2Xyz[9] = {0.4124, 0.3576, 0.1805, 0.2126, 0.7152, 0.0722, 0.0193, 0.1192, 0.9505};
+const double kXyz2Lms[9] = {0.4002, 0.7075, -0.0807, -0.2280, 1.1500, 0.0612, 0.0, 0.0, 0.9184};
+const double kLms2Ipt[9] = {0.4000, 0.4000, 0.2000, 4.4550, -4.8510, 0.3960, 0.8056, 0.3572, -1.1628};
+const double k709To2020[9] = {0.6274, 0.3293, 0.0433, 0.0691, 0.9195, 0.0114, 0.0164, 0.0880, 0.8956};
+
+void mul3(const double* x, const double* y, double* out) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       double s = 0.0;
-      for (int k = 0; k < 3; ++k) s += xyz2lms[i * 3 + k] * rgb2xyz[k * 3 + j];
-      P->a[i * 3 + j] = (float)s;
-      P->b[i * 3 + j] = (float)lms2ipt[i * 3 + j];
+      for (int k = 0; k < 3; ++k) s += x[i * 3 + k] * y[k * 3 + j];
+      out[i * 3 + j] = s;
     }
+}
+
+// inverse of a 3x3 matrix by its adjugate (the matrices here are far from
+// singular)
+void inv3(const double* m, double* out) {
+  const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  out[0] = c00 / det;
+  out[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+  out[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+  out[3] = c01 / det;
+  out[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+  out[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+  out[6] = c02 / det;
+  out[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+  out[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+// forward parameters; with `inverse` the matrices of the inverse transform
+// (a: LMS -> linear RGB or BT.2020 -> BT.709 primaries, b: IPT -> L'M'S')
+void make_params(int space, float gamma, ColourParams* P, bool inverse = false) {
+  double a[9], b[9], t[9];
+  if (space == MES_YCBCR2020CL) {
+    for (int i = 0; i < 9; ++i) a[i] = k709To2020[i];
+  } else {
+    mul3(kXyz2Lms, kRgb2Xyz, a);
+  }
+  for (int i = 0; i < 9; ++i) b[i] = kLms2Ipt[i];
+  if (inverse) {
+    inv3(a, t);
+    for (int i = 0; i < 9; ++i) a[i] = t[i];
+    inv3(b, t);
+    for (int i = 0; i < 9; ++i) b[i] = t[i];
+  }
+  for (int i = 0; i < 9; ++i) {
+    P->a[i] = (float)a[i];
+    P->b[i] = (float)b[i];
+  }
   P->gamma = gamma;
   P->space = space;
+}
+
+__device__ __forceinline__ float signed_pow(float v, float e) {
+  float a = fabsf(v);
+  return copysignf(a > 0.f ? powf(a, e) : 0.f, v);
+}
+
+// one pixel of the inverse transform: tensor channels -> R'G'B'
+__device__ __forceinline__ void invert_pixel(const ColourParams& P, float c0, float c1, float c2, float& r,
+                                             float& g, float& b) {
+  if (P.space == MES_YCBCR601) {
+    r = fmaf(1.402f, c2, c0);
+    b = fmaf(1.772f, c1, c0);
+    g = (c0 - 0.299f * r - 0.114f * b) * (1.f / 0.587f);
+    return;
+  }
+  float x, y, z;
+  if (P.space == MES_YCBCR2020CL) {
+    const float bp = fmaf(c1 <= 0.f ? kNb : kPb, c1, c0);
+    const float rp = fmaf(c2 <= 0.f ? kNr : kPr, c2, c0);
+    const float yc = oetf2020_inverse(c0), B = oetf2020_inverse(bp), R = oetf2020_inverse(rp);
+    x = R;
+    y = (yc - kKr20 * R - kKb20 * B) * (1.f / kKg20);
+    z = B;
+  } else {
+    x = signed_pow(fmaf(P.b[0], c0, fmaf(P.b[1], c1, P.b[2] * c2)), 1.f / 0.43f);
+    y = signed_pow(fmaf(P.b[3], c0, fmaf(P.b[4], c1, P.b[5] * c2)), 1.f / 0.43f);
+    z = signed_pow(fmaf(P.b[6], c0, fmaf(P.b[7], c1, P.b[8] * c2)), 1.f / 0.43f);
+  }
+  const float ig = 1.f / P.gamma;
+  r = signed_pow(fmaf(P.a[0], x, fmaf(P.a[1], y, P.a[2] * z)), ig);
+  g = signed_pow(fmaf(P.a[3], x, fmaf(P.a[4], y, P.a[5] * z)), ig);
+  b = signed_pow(fmaf(P.a[6], x, fmaf(P.a[7], y, P.a[8] * z)), ig);
+}
+
+__device__ __forceinline__ uint32_t to_u8(float v) {
+  // fmaxf/fminf drop a NaN, which then becomes 0
+  return (uint32_t)__float2int_rn(fminf(fmaxf(255.f * v, 0.f), 255.f));
+}
+
+constexpr int kInvPix = 4;
+
+// Inverse transform.  Fast path (npix % 4 == 0): a thread takes 4
+// consecutive pixels of one image, reads a float4 from each channel plane
+// and writes 12 bytes (three 32-bit words) and/or 12 floats (three float4).
+__global__ void __launch_bounds__(kThreads)
+colour_invert_kernel(const float* __restrict__ X, int64_t npix, int64_t K, ColourParams P,
+                     uint8_t* __restrict__ rgb8, float* __restrict__ rgbp) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (npix % kInvPix == 0) {
+    const int64_t per_img = npix / kInvPix;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per_img * K; t += stride) {
+      const int64_t k = t / per_img;
+      const int64_t p0 = (t - k * per_img) * kInvPix;
+      const float4 a = __ldg(reinterpret_cast<const float4*>(X + (3 * k + 0) * npix + p0));
+      const float4 bq = __ldg(reinterpret_cast<const float4*>(X + (3 * k + 1) * npix + p0));
+      const float4 cq = __ldg(reinterpret_cast<const float4*>(X + (3 * k + 2) * npix + p0));
+      const float c0[4] = {a.x, a.y, a.z, a.w}, c1[4] = {bq.x, bq.y, bq.z, bq.w}, c2[4] = {cq.x, cq.y, cq.z, cq.w};
+      float o[12];
+#pragma unroll
+      for (int i = 0; i < kInvPix; ++i) invert_pixel(P, c0[i], c1[i], c2[i], o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+      const int64_t base = (k * npix + p0) * 3;   // a multiple of 12
+      if (rgbp) {
+        float4* dst = reinterpret_cast<float4*>(rgbp + base);
+        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+      }
+      if (rgb8) {
+        uint32_t w[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          w[j] = to_u8(o[4 * j]) | (to_u8(o[4 * j + 1]) << 8) | (to_u8(o[4 * j + 2]) << 16) |
+                 (to_u8(o[4 * j + 3]) << 24);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(rgb8 + base);
+        dst[0] = w[0];
+        dst[1] = w[1];
+        dst[2] = w[2];
+      }
+    }
+  } else {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npix * K; t += stride) {
+      const int64_t k = t / npix;
+      const int64_t p = t - k * npix;
+      float r, g, b;
+      invert_pixel(P, X[(3 * k) * npix + p], X[(3 * k + 1) * npix + p], X[(3 * k + 2) * npix + p], r, g, b);
+      const int64_t base = (k * npix + p) * 3;
+      if (rgbp) {
+        rgbp[base] = r;
+        rgbp[base + 1] = g;
+        rgbp[base + 2] = b;
+      }
+      if (rgb8) {
+        rgb8[base] = (uint8_t)to_u8(r);
+        rgb8[base + 1] = (uint8_t)to_u8(g);
+        rgb8[base + 2] = (uint8_t)to_u8(b);
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -200,7 +366,7 @@ extern "C" mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_
   if (s1 < 1 || s2 < 1 || K < 1)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_convert: sizes must be >= 1 (got %lld %lld %lld)",
                      (long long)s1, (long long)s2, (long long)K);
-  if (space != MES_YCBCR601 && space != MES_IPT)
+  if (space != MES_YCBCR601 && space != MES_IPT && space != MES_YCBCR2020CL)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_convert: unknown colour space %d", space);
   if (!(gamma > 0.f)) return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_convert: gamma must be > 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -208,4 +374,27 @@ extern "C" mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_
   double* partials = nullptr;
   if (norm2) MES_TRY(scratch.alloc(&partials, mes::colour_grid(s1 * s2, K)));
   return mes::colour_launch(rgb8, s1, s2, K, space, gamma, out, partials, norm2, st);
+}
+
+extern "C" mes_status mes_colour_invert(const float* X, int64_t s1, int64_t s2, int64_t K, int space,
+                                        float gamma, uint8_t* rgb8, float* rgbp, void* stream) {
+  mes::clear_error();
+  if (!X || (!rgb8 && !rgbp))
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: null X or no output");
+  if (s1 < 1 || s2 < 1 || K < 1)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: sizes must be >= 1 (got %lld %lld %lld)",
+                     (long long)s1, (long long)s2, (long long)K);
+  if (space != MES_YCBCR601 && space != MES_IPT && space != MES_YCBCR2020CL)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: unknown colour space %d", space);
+  if (!(gamma > 0.f)) return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: gamma must be > 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ColourParams P;
+  make_params(space, gamma, &P, true);
+  const int64_t npix = s1 * s2;
+  const int64_t work = (npix % kInvPix == 0) ? npix / kInvPix * K : npix * K;
+  const unsigned grid = mes::grid_for(work, kThreads, (int64_t)mes::sm_count() * 8);
+  mes::ProfScope prof("colour_invert", st, 0.0, (12.0 + (rgb8 ? 3.0 : 0.0) + (rgbp ? 12.0 : 0.0)) * npix * K);
+  colour_invert_kernel<<<grid, kThreads, 0, st>>>(X, npix, K, P, rgb8, rgbp);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
 }

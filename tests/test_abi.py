@@ -149,3 +149,14 @@ def test_init_option_validated_without_gpu(lib):
     lib.mes_tucker_als_workspace_size(4, dims, ranks, ctypes.byref(o0), ctypes.byref(a))
     lib.mes_tucker_als_workspace_size(4, dims, ranks, ctypes.byref(o1), ctypes.byref(b))
     assert a.value == b.value
+
+
+def test_colour_invert_validation_without_gpu(lib):
+    bogus = ctypes.c_void_p(16)
+    g = ctypes.c_float(2.2)
+    assert lib.mes_colour_invert(None, 4, 4, 1, 0, g, bogus, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 0, g, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 0, 4, 1, 0, g, bogus, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 3, g, bogus, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 2, ctypes.c_float(0.0), bogus, None, None) == 1
+    assert lib.mes_colour_convert(bogus, 4, 4, 1, 3, g, bogus, None, None) == 1

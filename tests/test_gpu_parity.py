@@ -65,7 +65,7 @@ def gap_and_sin(T, ref_factors, n, U_gpu):
 
 
 # ---------------------------------------------------------------- colour
-@pytest.mark.parametrize("space,tol", [("ycbcr", 2e-7), ("ipt", 2e-5)])
+@pytest.mark.parametrize("space,tol", [("ycbcr", 2e-7), ("ipt", 2e-5), ("ycbcr2020cl", 1e-6)])
 @pytest.mark.parametrize("shape", [(64, 48, 6), (37, 23, 3), (8, 1, 1)])
 def test_colour_matches_oracle(mes, space, tol, shape):
     s1, s2, K = shape
@@ -80,6 +80,49 @@ def test_colour_matches_oracle(mes, space, tol, shape):
     assert got.shape == want.shape
     assert np.abs(got - want).max() < tol
     assert abs(float(n2.cpu()) - colour.frobenius2(want)) <= 1e-5 * colour.frobenius2(want)
+
+
+@pytest.mark.parametrize("space", ["ycbcr", "ipt", "ycbcr2020cl"])
+@pytest.mark.parametrize("shape", [(64, 48, 6), (37, 23, 3), (7, 1, 2)])
+def test_colour_invert_matches_oracle(mes, space, shape):
+    """Inverse transform of a perturbed tensor (as a reconstruction gives:
+    noise of 0.02 takes some pixels out of gamut) against the oracle's FP64
+    inverse of the same FP32 input.  R'G'B' within 2e-5 where R' > 0.05; near
+    black the power 1/gamma magnifies FP32 round-off, so there the linear
+    values (R')^gamma are compared, within 1e-6.  Bytes: equal, except within
+    0.2 of a rounding boundary or below 0.06, where they may differ by one."""
+    s1, s2, K = shape
+    rng = np.random.default_rng(s1 * 13 + K)
+    img = rng.integers(0, 256, size=(K, s2, s1, 3), dtype=np.uint8)
+    T = colour.colour_convert(img, space) + 0.02 * rng.standard_normal((s1, s2, 3, K))
+    T32 = T.astype(np.float32)
+    u8, fp = mes.colour_invert(to_torch(T32), space, want_float=True)
+    torch.cuda.synchronize()
+    want = colour.colour_invert(T32.astype(np.float64), space)
+    got = fp.cpu().numpy().astype(np.float64)
+    big = np.abs(want) > 0.05
+    assert np.abs(got - want)[big].max() < 2e-5
+    lin = lambda v: np.sign(v) * np.abs(v) ** 2.2 if space != "ycbcr" else v
+    assert np.abs(lin(got) - lin(want))[~big].max(initial=0.0) < 1e-6
+    gb, wb = u8.cpu().numpy().astype(int), colour.to_u8(want).astype(int)
+    x = np.clip(255.0 * want, 0, 255)
+    near = (np.abs(x - np.floor(x) - 0.5) < 0.2) | (want < 0.06)
+    assert np.array_equal(gb[~near], wb[~near])
+    assert np.abs(gb - wb).max() <= 1
+
+
+@pytest.mark.parametrize("space", ["ycbcr", "ipt", "ycbcr2020cl"])
+@pytest.mark.parametrize("shape", [(64, 48, 6), (37, 23, 3)])
+def test_colour_round_trip_recovers_the_bytes(mes, space, shape):
+    s1, s2, K = shape
+    rng = np.random.default_rng(s2 * 5 + K)
+    img = rng.integers(0, 256, size=(K, s2, s1, 3), dtype=np.uint8)
+    img[0, 0, :3] = [[0, 0, 0], [255, 255, 255], [0, 0, 255]]
+    t = torch.from_numpy(img).to(DEV)
+    X, _ = mes.colour_convert(t, space)
+    back, _ = mes.colour_invert(X, space)
+    torch.cuda.synchronize()
+    assert torch.equal(back, t)
 
 
 def test_colour_norm_is_reproducible(mes):
