@@ -124,12 +124,19 @@ mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_t s2, int64
  *               each channel clamp(rint(255 R'), 0, 255), ties to even.
  *  rgbp   [out] nullable; the same images as FP32 R'G'B' before rounding and
  *               clamping (interleaved like rgb8).
- * Errors: MES_ERR_INVALID_ARG for a null X, both outputs null, non-positive
- *         sizes, an unknown space or gamma <= 0; MES_ERR_CUDA on a launch
+ *  ref8   [in]  nullable; 8-bit images in the layout of rgb8 (e.g. the
+ *               input of mes_colour_convert).  Given together with sse8.
+ *  sse8   [out] nullable device double: sum over all bytes of (out - ref8)^2,
+ *               exact (integer sums), for the PSNR of the decoded views
+ *               (Figs. 3 and 4 report it per view after coding).
+ * Errors: MES_ERR_INVALID_ARG for a null X, no output at all (rgb8, rgbp,
+ *         sse8 all null), only one of ref8 / sse8, non-positive sizes, an
+ *         unknown space or gamma <= 0; MES_ERR_OOM; MES_ERR_CUDA on a launch
  *         failure.  A NaN gives byte 0, not an error.
  */
 mes_status mes_colour_invert(const float* X, int64_t s1, int64_t s2, int64_t K, int space,
-                             float gamma, uint8_t* rgb8, float* rgbp, void* stream);
+                             float gamma, uint8_t* rgb8, float* rgbp, const uint8_t* ref8,
+                             double* sse8, void* stream);
 
 /*
  * Options of mes_tucker_als.  Zero-initialise and set what you need; a NULL

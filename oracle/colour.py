@@ -189,6 +189,14 @@ def to_u8(rgbp: np.ndarray) -> np.ndarray:
     return np.clip(np.rint(255.0 * np.asarray(rgbp)), 0, 255).astype(np.uint8)
 
 
+def psnr8(ref8: np.ndarray, out8: np.ndarray) -> float:
+    """PSNR of 8-bit views over all their bytes, peak 255 (the quality
+    measure of Figs. 3 and 4)."""
+    d = np.asarray(ref8, dtype=np.float64) - np.asarray(out8, dtype=np.float64)
+    mse = float(np.mean(d * d))
+    return float("inf") if mse == 0.0 else 10.0 * np.log10(255.0 ** 2 / mse)
+
+
 def frobenius2(T: np.ndarray) -> float:
     """||T||_F^2, the squared norm used by the fit."""
     return float(np.sum(np.square(T, dtype=np.float64)))

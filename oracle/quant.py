@@ -45,6 +45,12 @@ def planes_of(core: np.ndarray) -> np.ndarray:
     return np.transpose(flat, (2, 0, 1))
 
 
+def core_of_planes(planes: np.ndarray, ranks) -> np.ndarray:
+    """Planes (P, R1, R2) -> core of shape `ranks`: the inverse of planes_of."""
+    flat = np.transpose(np.asarray(planes), (1, 2, 0))
+    return np.reshape(flat, tuple(int(r) for r in ranks), order="F")
+
+
 def quantize_planes(planes: np.ndarray, bits: int):
     """FP32 planes (P, R1, R2) -> (int16 codes (P, R1, R2), FP32 scales (P,))."""
     if not 2 <= bits <= 16:

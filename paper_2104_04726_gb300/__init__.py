@@ -18,7 +18,7 @@ from typing import Sequence
 
 from . import _lib
 
-__all__ = ["colour_invert", "colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequantize_core",
+__all__ = ["colour_invert", "rate_bits", "rate_sweep", "colour_convert", "tucker_als", "reconstruct", "quantize_core", "dequantize_core",
            "version", "torch_shape", "paper_dims", "PRECISIONS", "SPACES", "MesError"]
 
 MesError = _lib.MesError
@@ -85,11 +85,13 @@ def colour_convert(rgb8, space: str = "ycbcr", gamma: float = 2.2, out=None, nor
 
 
 def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=None, want_u8: bool = True,
-                  want_float: bool = False):
+                  want_float: bool = False, ref8=None):
     """Inverse colour transform: float32 CUDA tensor of torch shape
     (K, 3, s2, s1) (paper dims (s1, s2, 3, K)) -> images (K, s2, s1, 3):
     uint8 (clamp(rint(255 R'))) and/or float32 R'G'B'.  Returns (rgb8, rgbp),
-    None for an output not asked for."""
+    None for an output not asked for; with `ref8` (uint8 images of the same
+    shape) returns (rgb8, rgbp, sse8), sse8 a float64 CUDA scalar with the
+    exact sum of squared byte differences."""
     torch = _torch()
     _need(X, torch.float32, "X")
     K, c, s2, s1 = X.shape
@@ -99,11 +101,17 @@ def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=N
         rgb8 = torch.empty((K, s2, s1, 3), dtype=torch.uint8, device=X.device)
     if want_float and rgbp is None:
         rgbp = torch.empty((K, s2, s1, 3), dtype=torch.float32, device=X.device)
+    sse8 = None
+    if ref8 is not None:
+        _need(ref8, torch.uint8, "ref8")
+        if tuple(ref8.shape) != (K, s2, s1, 3):
+            raise ValueError("ref8 must have shape (K, s2, s1, 3)")
+        sse8 = torch.empty((), dtype=torch.float64, device=X.device)
     lib = _lib.load()
     st = lib.mes_colour_invert(_ptr(X), s1, s2, K, SPACES[space], ctypes.c_float(gamma), _ptr(rgb8),
-                               _ptr(rgbp), _stream())
+                               _ptr(rgbp), _ptr(ref8), _ptr(sse8), _stream())
     _lib.check(st, "mes_colour_invert")
-    return rgb8, rgbp
+    return (rgb8, rgbp) if ref8 is None else (rgb8, rgbp, sse8)
 
 
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
@@ -221,6 +229,56 @@ def dequantize_core(q, scales, ranks: Sequence[int]):
     _lib.check(st, "mes_dequantize_core")
     return core
 
+
+
+def rate_bits(dims: Sequence[int], ranks: Sequence[int], bits: int = 0, factor_bits: int = 16) -> int:
+    """Bits of the coded representation before entropy coding: the core at
+    `bits` per entry (0: FP32) plus one FP32 scale per quantiser plane, and
+    the factors at `factor_bits` per entry.  The paper codes the rank and
+    the quantisation of the core as the rate knob (abstract, Section I) but
+    fixes no format; this is the count a fixed-length code would take."""
+    n_core = 1
+    for r in ranks:
+        n_core *= int(r)
+    planes = 1
+    for r in ranks[2:]:
+        planes *= int(r)
+    core = n_core * (bits if bits else 32) + (planes * 32 if bits else 0)
+    return core + sum(int(d) * int(r) for d, r in zip(dims, ranks)) * factor_bits
+
+
+def rate_sweep(rgb8, space: str, rank_grid, bits_grid, max_iters: int = 20, tol: float = 0.0,
+               precision: str = "fp32", gamma: float = 2.2, factor_bits: int = 16, **als_opts):
+    """Rate-distortion sweep over core ranks x quantiser bits (the in-scope
+    half of Figs. 3 and 4): one decomposition per rank tuple, then per bit
+    depth quantise -> dequantise -> reconstruct -> inverse colour -> PSNR of
+    the 8-bit views against the input.  rgb8: uint8 CUDA tensor (K, s2, s1,
+    3); bits 0 keeps the FP32 core.  Returns a list of dicts with ranks,
+    bits, bpp (rate_bits per pixel of the stack), psnr (dB, over all bytes)
+    and fit (of the unquantised decomposition).  Further keyword arguments
+    go to tucker_als."""
+    import math
+    K, s2, s1, _ = rgb8.shape
+    dims = [s1, s2, 3, K]
+    X, _ = colour_convert(rgb8, space, gamma)
+    n_bytes = s1 * s2 * K * 3
+    rows = []
+    for ranks in rank_grid:
+        ranks = [int(r) for r in ranks]
+        res = tucker_als(X, dims, ranks, max_iters=max_iters, tol=tol, precision=precision, **als_opts)
+        fit = float(res["fit"].cpu())
+        for bits in bits_grid:
+            core = res["core"]
+            if bits:
+                q, sc = quantize_core(core, ranks, bits)
+                core = dequantize_core(q, sc, ranks)
+            Xh = reconstruct(core, res["factors"], dims, ranks, precision=precision)
+            _, _, sse8 = colour_invert(Xh, space, gamma, want_u8=False, ref8=rgb8)
+            sse = float(sse8.cpu())
+            psnr = math.inf if sse == 0.0 else 10.0 * math.log10(255.0 ** 2 * n_bytes / sse)
+            rows.append({"ranks": ranks, "bits": int(bits), "psnr": psnr, "fit": fit,
+                         "bpp": rate_bits(dims, ranks, bits, factor_bits) / (s1 * s2 * K)})
+    return rows
 
 class Problem:
     """One stack for the batched and served forms: device buffers for the

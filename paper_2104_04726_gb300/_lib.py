@@ -32,7 +32,7 @@ SIGNATURES = {
     "mes_colour_convert": (_c.c_int, [_p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _c.c_float,
                                       _p, _p, _p]),
     "mes_colour_invert": (_c.c_int, [_p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _c.c_float,
-                                     _p, _p, _p]),
+                                     _p, _p, _p, _p, _p]),
     "mes_tucker_als": (_c.c_int, [_p, _c.c_int, _i64p, _i64p, _c.c_int, _c.c_double, _p,
                                   _c.POINTER(_p), _p, _p, _p]),
     "mes_tucker_als_workspace_size": (_c.c_int, [_c.c_int, _i64p, _i64p, _p, _c.POINTER(_c.c_size_t)]),

@@ -271,8 +271,10 @@ constexpr int kInvPix = 4;
 // and writes 12 bytes (three 32-bit words) and/or 12 floats (three float4).
 __global__ void __launch_bounds__(kThreads)
 colour_invert_kernel(const float* __restrict__ X, int64_t npix, int64_t K, ColourParams P,
-                     uint8_t* __restrict__ rgb8, float* __restrict__ rgbp) {
+                     uint8_t* __restrict__ rgb8, float* __restrict__ rgbp, const uint8_t* __restrict__ ref8,
+                     double* __restrict__ partials) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long err = 0;   // sum of squared byte differences, exact
   if (npix % kInvPix == 0) {
     const int64_t per_img = npix / kInvPix;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < per_img * K; t += stride) {
@@ -292,16 +294,30 @@ colour_invert_kernel(const float* __restrict__ X, int64_t npix, int64_t K, Colou
         dst[1] = make_float4(o[4], o[5], o[6], o[7]);
         dst[2] = make_float4(o[8], o[9], o[10], o[11]);
       }
-      if (rgb8) {
+      if (rgb8 || ref8) {
         uint32_t w[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
           w[j] = to_u8(o[4 * j]) | (to_u8(o[4 * j + 1]) << 8) | (to_u8(o[4 * j + 2]) << 16) |
                  (to_u8(o[4 * j + 3]) << 24);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(rgb8 + base);
-        dst[0] = w[0];
-        dst[1] = w[1];
-        dst[2] = w[2];
+        if (rgb8) {
+          uint32_t* dst = reinterpret_cast<uint32_t*>(rgb8 + base);
+          dst[0] = w[0];
+          dst[1] = w[1];
+          dst[2] = w[2];
+        }
+        if (ref8) {
+          const uint32_t* r = reinterpret_cast<const uint32_t*>(ref8 + base);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const uint32_t v = __ldg(r + j);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int d = (int)((w[j] >> (8 * q)) & 0xff) - (int)((v >> (8 * q)) & 0xff);
+              err += (unsigned long long)(d * d);
+            }
+          }
+        }
       }
     }
   } else {
@@ -316,12 +332,26 @@ colour_invert_kernel(const float* __restrict__ X, int64_t npix, int64_t K, Colou
         rgbp[base + 1] = g;
         rgbp[base + 2] = b;
       }
+      const uint32_t o8[3] = {to_u8(r), to_u8(g), to_u8(b)};
       if (rgb8) {
-        rgb8[base] = (uint8_t)to_u8(r);
-        rgb8[base + 1] = (uint8_t)to_u8(g);
-        rgb8[base + 2] = (uint8_t)to_u8(b);
+        rgb8[base] = (uint8_t)o8[0];
+        rgb8[base + 1] = (uint8_t)o8[1];
+        rgb8[base + 2] = (uint8_t)o8[2];
+      }
+      if (ref8) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int d = (int)o8[c] - (int)ref8[base + c];
+          err += (unsigned long long)(d * d);
+        }
       }
     }
+  }
+  if (partials) {
+    // per-thread sums are below 2^53 for any image count that fits in memory,
+    // so the FP64 block sum is exact and the result reproducible
+    double t = block_sum((double)err);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
@@ -377,10 +407,13 @@ extern "C" mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_
 }
 
 extern "C" mes_status mes_colour_invert(const float* X, int64_t s1, int64_t s2, int64_t K, int space,
-                                        float gamma, uint8_t* rgb8, float* rgbp, void* stream) {
+                                        float gamma, uint8_t* rgb8, float* rgbp, const uint8_t* ref8,
+                                        double* sse8, void* stream) {
   mes::clear_error();
-  if (!X || (!rgb8 && !rgbp))
+  if (!X || (!rgb8 && !rgbp && !sse8))
     return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: null X or no output");
+  if (!ref8 != !sse8)
+    return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: ref8 and sse8 go together");
   if (s1 < 1 || s2 < 1 || K < 1)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_invert: sizes must be >= 1 (got %lld %lld %lld)",
                      (long long)s1, (long long)s2, (long long)K);
@@ -394,7 +427,14 @@ extern "C" mes_status mes_colour_invert(const float* X, int64_t s1, int64_t s2, 
   const int64_t work = (npix % kInvPix == 0) ? npix / kInvPix * K : npix * K;
   const unsigned grid = mes::grid_for(work, kThreads, (int64_t)mes::sm_count() * 8);
   mes::ProfScope prof("colour_invert", st, 0.0, (12.0 + (rgb8 ? 3.0 : 0.0) + (rgbp ? 12.0 : 0.0)) * npix * K);
-  colour_invert_kernel<<<grid, kThreads, 0, st>>>(X, npix, K, P, rgb8, rgbp);
+  double* partials = nullptr;
+  mes::Scratch scratch(st);
+  if (sse8) MES_TRY(scratch.alloc(&partials, grid));
+  colour_invert_kernel<<<grid, kThreads, 0, st>>>(X, npix, K, P, rgb8, rgbp, ref8, partials);
   MES_LAUNCH_CHECK();
+  if (sse8) {
+    sum_partials_kernel<<<1, kThreads, 0, st>>>(partials, (int)grid, sse8);
+    MES_LAUNCH_CHECK();
+  }
   return MES_OK;
 }

@@ -154,9 +154,20 @@ def test_init_option_validated_without_gpu(lib):
 def test_colour_invert_validation_without_gpu(lib):
     bogus = ctypes.c_void_p(16)
     g = ctypes.c_float(2.2)
-    assert lib.mes_colour_invert(None, 4, 4, 1, 0, g, bogus, None, None) == 1
-    assert lib.mes_colour_invert(bogus, 4, 4, 1, 0, g, None, None, None) == 1
-    assert lib.mes_colour_invert(bogus, 0, 4, 1, 0, g, bogus, None, None) == 1
-    assert lib.mes_colour_invert(bogus, 4, 4, 1, 3, g, bogus, None, None) == 1
-    assert lib.mes_colour_invert(bogus, 4, 4, 1, 2, ctypes.c_float(0.0), bogus, None, None) == 1
+    assert lib.mes_colour_invert(None, 4, 4, 1, 0, g, bogus, None, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 0, g, None, None, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 0, 4, 1, 0, g, bogus, None, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 3, g, bogus, None, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 2, ctypes.c_float(0.0), bogus, None, None, None, None) == 1
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 2, g, bogus, None, bogus, None, None) == 1   # ref8 without sse8
+    assert lib.mes_colour_invert(bogus, 4, 4, 1, 2, g, None, None, None, bogus, None) == 1    # sse8 without ref8
     assert lib.mes_colour_convert(bogus, 4, 4, 1, 3, g, bogus, None, None) == 1
+
+
+def test_rate_bits_counts_core_scales_and_factors():
+    import paper_2104_04726_gb300 as mes
+    dims, ranks = [64, 48, 3, 6], [16, 12, 3, 6]
+    factors = 64 * 16 + 48 * 12 + 3 * 3 + 6 * 6
+    assert mes.rate_bits(dims, ranks, 8) == 16 * 12 * 18 * 8 + 18 * 32 + factors * 16
+    assert mes.rate_bits(dims, ranks, 0) == 16 * 12 * 18 * 32 + factors * 16
+    assert mes.rate_bits(dims, ranks, 4, factor_bits=8) == 16 * 12 * 18 * 4 + 18 * 32 + factors * 8

@@ -546,3 +546,33 @@ def test_interlaced_init_converges_to_the_scene_fit(mes):
         res = _run(mes, T, cfg["ranks"], cfg["iters"], cfg["tol"], inner_iters=4, init=init)
         fit = float(res["fit"].cpu())
         assert abs(fit - ref.fit) / ref.fit < 1e-5, (init, fit, ref.fit)
+
+
+
+def test_rate_sweep_matches_the_oracle_pipeline(mes):
+    """Ranks x bits sweep on the 64x48 scene against the oracle's own chain
+    (HOOI, per-plane quantiser, dequantiser, Eq. 1, inverse colour, 8-bit
+    PSNR): PSNR within 0.05 dB of the oracle's, rising with the bit depth and
+    with the ranks."""
+    cfg, img = _scene("small_64x48")
+    space = cfg["space"]
+    grid = [(8, 6, 3, 6), (16, 12, 3, 6)]
+    bits = [4, 8, 0]
+    rows = mes.rate_sweep(torch.from_numpy(img).to(DEV), space, grid, bits, max_iters=10, tol=1e-8,
+                          inner_iters=4)
+    T = colour.colour_convert(img, space)
+    for row in rows:
+        ref = tucker.hooi(T, row["ranks"], 10, 1e-8)
+        core = ref.core
+        if row["bits"]:
+            q, sc = quant.quantize_planes(quant.planes_of(core.astype(np.float32)), row["bits"])
+            core = quant.core_of_planes(quant.dequantize_planes(q, sc), row["ranks"]).astype(np.float64)
+        Xh = tucker.reconstruct(core, ref.factors)
+        want = colour.psnr8(img, colour.to_u8(colour.colour_invert(Xh, space)))
+        print(row, f"oracle {want:.4f}")
+        assert abs(row["psnr"] - want) < 0.05, (row, want)
+    by = {(tuple(r["ranks"]), r["bits"]): r["psnr"] for r in rows}
+    for g in grid:
+        assert by[(g, 4)] < by[(g, 8)] <= by[(g, 0)] + 0.05
+    for b in bits:
+        assert by[(grid[0], b)] < by[(grid[1], b)]

@@ -167,3 +167,13 @@ def test_inverse_transforms_recover_the_images(space):
 def test_to_u8_rounds_half_to_even_and_clamps():
     x = np.array([-0.1, 0.0, 0.5 / 255, 1.5 / 255, 2.5 / 255, 254.5 / 255, 1.0, 1.2])
     assert colour.to_u8(x).tolist() == [0, 0, 0, 2, 2, 254, 255, 255]
+
+
+def test_psnr8_definition():
+    a = np.zeros((2, 3, 4, 3), dtype=np.uint8)
+    b = a.copy()
+    assert colour.psnr8(a, b) == float("inf")
+    b[0, 0, 0, 0] = 1            # one byte off by one of n = 72: mse = 1/72
+    assert abs(colour.psnr8(a, b) - 10 * np.log10(255.0 ** 2 * 72)) < 1e-12
+    b[:] = 255                   # every byte off by the peak: 0 dB
+    assert colour.psnr8(a, b) == 0.0

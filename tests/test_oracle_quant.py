@@ -63,3 +63,12 @@ def test_bits_range():
         quant.quantize_planes(np.zeros((1, 2, 2), np.float32), 1)
     with pytest.raises(ValueError):
         quant.quantize_planes(np.zeros((1, 2, 2), np.float32), 17)
+
+
+def test_core_of_planes_inverts_planes_of():
+    rng = np.random.default_rng(5)
+    for ranks in ((4, 3, 2, 5), (3, 2), (2, 2, 3)):
+        core = rng.standard_normal(ranks)
+        planes = quant.planes_of(core)
+        assert planes.shape == (quant.num_planes(ranks), ranks[0], ranks[1])
+        assert np.array_equal(quant.core_of_planes(planes, ranks), core)
