@@ -39,9 +39,12 @@ __device__ __forceinline__ float oetf2020_inverse(float e) {
 constexpr int kThreads = 256;
 constexpr int kPix = 8;
 
+// accurate powf (not the fast log2/exp2 pair): the inverse transform must
+// recover the 8-bit input exactly, and the power 1/0.43 of the inverse
+// magnifies forward errors on saturated colours with a dark channel
 __device__ __forceinline__ float signed_pow043(float v) {
   float a = fabsf(v);
-  float p = (a > 0.f) ? exp2f(0.43f * __log2f(a)) : 0.f;
+  float p = (a > 0.f) ? powf(a, 0.43f) : 0.f;
   return copysignf(p, v);
 }
 
