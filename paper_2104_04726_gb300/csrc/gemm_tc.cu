@@ -112,14 +112,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// L2 prefetch of a tile (no shared memory, no completion): issued a few
-// k-tiles ahead of the ring so the later load finds its tile in L2
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
-  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(map), "r"(c0),
-               "r"(c1), "r"(c2), "r"(c3)
-               : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -265,22 +257,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    // With two or three stages the ring covers little of the DRAM latency;
-    // the tile kPrefetch k-tiles ahead is requested into L2 when a stage is
-    // loaded, so the ring's loads mostly hit L2.
-    constexpr int kPrefetch = 4;
-    auto prefetch = [&](int i) {
-      const int kt = kt_begin + i;
-      const int kh = kt / args.k_tiles_lo;
-      const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
-      tma_prefetch_4d(&mapA, kl, (int)m0, kh, args.a_batched ? b : 0);
-      tma_prefetch_4d(&mapB, kl, (int)n0, kh, args.b_batched ? b : 0);
-      if (KIND == 2) {
-        tma_prefetch_4d(&mapA2, kl, (int)m0, kh, args.a_batched ? b : 0);
-        tma_prefetch_4d(&mapB2, kl, (int)n0, kh, args.b_batched ? b : 0);
-      }
-    };
-    for (int i = STAGES; i < STAGES + kPrefetch && i < nkt; ++i) prefetch(i);
     int stage = 0;
     uint32_t phase = 0;
     for (int i = 0; i < nkt; ++i) {
@@ -288,7 +264,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         ok = false;
         break;
       }
-      if (i + STAGES + kPrefetch < nkt) prefetch(i + STAGES + kPrefetch);
       const int kt = kt_begin + i;
       const int kh = kt / args.k_tiles_lo;
       const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
