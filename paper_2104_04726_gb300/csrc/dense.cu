@@ -1233,73 +1233,96 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
       else buf[(e & 31) * kTLd + (e >> 5)] = pre[q];
     }
   };
-  float pre[kWPer];
+  // Three tiles of look-ahead in registers: a tile's products take about
+  // half an L2 round trip, so a single prefetched tile stalled every step.
+  // Four register slots rotate through the stream with static names (the
+  // loop is unrolled by four; a copy between slots would wait on the load).
+  float pre0[kWPer], pre1[kWPer], pre2[kWPer], pre3[kWPer];
   int cbn = 0, jn = 0;   // next tile to load
-  tile_load(cbn, jn, pre);
+  auto advance = [&]() {
+    if (++jn > cbn) { ++cbn; jn = 0; }
+  };
+  tile_load(cbn, jn, pre0);
+  advance();
+  if (cbn < nb) tile_load(cbn, jn, pre1);
+  advance();
+  if (cbn < nb) tile_load(cbn, jn, pre2);
+  advance();
   int bsel = 0;
-  for (int cb = 0; cb < nb; ++cb) {
+  int cb = 0, j = 0;   // tile being consumed
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
+  // consume the tile in `cur` (block cb, tile j), refill `nxt` three ahead
+  auto step = [&](const float (&cur)[kWPer], float (&nxt)[kWPer]) {
     const int c0 = cb * PB;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int j = 0; j <= cb; ++j) {
-      float* buf = Lk + bsel * (PB * kTLd);
-      tile_store(buf, cb, j, pre);
-      __syncthreads();   // tile visible; every thread is done with the other buffer
-      // prefetch the next tile of the stream into registers
-      if (++jn > cbn) { ++cbn; jn = 0; }
-      if (cbn < nb) tile_load(cbn, jn, pre);
-      if (j < cb) {
-        const int k0 = PB * j;
+    float* buf = Lk + bsel * (PB * kTLd);
+    tile_store(buf, cb, j, cur);
+    __syncthreads();   // tile visible; every thread is done with the other buffer
+    if (cbn < nb) tile_load(cbn, jn, nxt);
+    advance();
+    if (j < cb) {
+      const int k0 = PB * j;
 #pragma unroll 8
-        for (int k = 0; k < PB; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
-          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
-          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a4[i], b4[jj], acc[i][jj]);
-        }
-      } else {
-        // diagonal block: x := (x - acc) Linv^T; the rows are this warp's own
-        const int kmax = min(PB, r - c0);
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int c = c0 + 4 * cg + jj;
-          if (c < r)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][jj];
-        }
-        __syncwarp();
-        float x[4][4];
+      for (int k = 0; k < PB; ++k) {
+        const float4 av = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
+        const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) x[i][jj] = 0.f;
-        for (int k = 0; k < kmax; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
-          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
-          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) x[i][jj] = fmaf(a4[i], b4[jj], x[i][jj]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int c = c0 + 4 * cg + jj;
-          if (c < r)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][jj];
-        }
-        __syncwarp();
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a4[i], b4[jj], acc[i][jj]);
       }
-      bsel ^= 1;
+    } else {
+      // diagonal block: x := (x - acc) Linv^T; the rows are this warp's own
+      const int kmax = min(PB, r - c0);
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = c0 + 4 * cg + jj;
+        if (c < r)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][jj];
+      }
+      __syncwarp();
+      float x[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x[i][jj] = 0.f;
+      for (int k = 0; k < kmax; ++k) {
+        const float4 av = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
+        const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) x[i][jj] = fmaf(a4[i], b4[jj], x[i][jj]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = c0 + 4 * cg + jj;
+        if (c < r)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][jj];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
     }
+    bsel ^= 1;
+    if (++j > cb) { ++cb; j = 0; }
+  };
+  const int ntiles = nb * (nb + 1) / 2;
+  for (int q = 0; q < ntiles; q += 4) {
+    step(pre0, pre3);
+    if (q + 1 < ntiles) step(pre1, pre0);
+    if (q + 2 < ntiles) step(pre2, pre1);
+    if (q + 3 < ntiles) step(pre3, pre2);
   }
   __syncthreads();
   if ((s & 3) == 0 && row0 + kWRows <= s && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
