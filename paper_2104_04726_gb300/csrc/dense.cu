@@ -602,21 +602,29 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
       while (kmin <= p) kmin += kCL;
       if (kmin < nb) {
         // panel p, rows g_lo .. rp-1: the owner uses its own copy, the
-        // others read it from L (column-major, written before the barrier)
+        // others copy it from the owner's shared memory (distributed shared
+        // memory, same row layout; final since the owner factored it before
+        // the last cluster barrier, and never written again in this attempt)
         const int owner = p % kCL, g_lo = PB * kmin;
         const float* P;
+        const float* own = store + (dsm_slot_offset(owner, p / kCL, rp) + (g_lo - PB * p)) * LD;
         if (owner == rank) {
-          P = store + (dsm_slot_offset(rank, p / kCL, rp) + (g_lo - PB * p)) * LD;
+          P = own;
         } else {
-          const int nrows = rp - g_lo;
-          const float* Lp = Lout + (int64_t)r * (PB * p) + g_lo;
-          for (int i = t; i < nrows; i += kChol) {
-            const bool in = g_lo + i < r;
-            float v[PB];
+          const int n = (rp - g_lo) * PB;
+          const float* R = cluster.map_shared_rank(const_cast<float*>(own), owner);
+          for (int e0 = t; e0 < n; e0 += 4 * kChol) {
+            float v[4];
 #pragma unroll
-            for (int c = 0; c < PB; ++c) v[c] = in ? __ldcg(Lp + i + (int64_t)r * c) : 0.f;
+            for (int u = 0; u < 4; ++u) {
+              const int e = e0 + u * kChol;
+              v[u] = e < n ? R[(e >> 5) * LD + (e & 31)] : 0.f;
+            }
 #pragma unroll
-            for (int c = 0; c < PB; ++c) Pl_alloc[i * LD + c] = v[c];
+            for (int u = 0; u < 4; ++u) {
+              const int e = e0 + u * kChol;
+              if (e < n) Pl_alloc[(e >> 5) * LD + (e & 31)] = v[u];
+            }
           }
           P = Pl_alloc;
         }
@@ -1233,96 +1241,73 @@ trsm_wide_kernel(const float* __restrict__ W, int64_t s, int r, const float* __r
       else buf[(e & 31) * kTLd + (e >> 5)] = pre[q];
     }
   };
-  // Three tiles of look-ahead in registers: a tile's products take about
-  // half an L2 round trip, so a single prefetched tile stalled every step.
-  // Four register slots rotate through the stream with static names (the
-  // loop is unrolled by four; a copy between slots would wait on the load).
-  float pre0[kWPer], pre1[kWPer], pre2[kWPer], pre3[kWPer];
+  float pre[kWPer];
   int cbn = 0, jn = 0;   // next tile to load
-  auto advance = [&]() {
-    if (++jn > cbn) { ++cbn; jn = 0; }
-  };
-  tile_load(cbn, jn, pre0);
-  advance();
-  if (cbn < nb) tile_load(cbn, jn, pre1);
-  advance();
-  if (cbn < nb) tile_load(cbn, jn, pre2);
-  advance();
+  tile_load(cbn, jn, pre);
   int bsel = 0;
-  int cb = 0, j = 0;   // tile being consumed
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
-  // consume the tile in `cur` (block cb, tile j), refill `nxt` three ahead
-  auto step = [&](const float (&cur)[kWPer], float (&nxt)[kWPer]) {
+  for (int cb = 0; cb < nb; ++cb) {
     const int c0 = cb * PB;
-    float* buf = Lk + bsel * (PB * kTLd);
-    tile_store(buf, cb, j, cur);
-    __syncthreads();   // tile visible; every thread is done with the other buffer
-    if (cbn < nb) tile_load(cbn, jn, nxt);
-    advance();
-    if (j < cb) {
-      const int k0 = PB * j;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j <= cb; ++j) {
+      float* buf = Lk + bsel * (PB * kTLd);
+      tile_store(buf, cb, j, pre);
+      __syncthreads();   // tile visible; every thread is done with the other buffer
+      // prefetch the next tile of the stream into registers
+      if (++jn > cbn) { ++cbn; jn = 0; }
+      if (cbn < nb) tile_load(cbn, jn, pre);
+      if (j < cb) {
+        const int k0 = PB * j;
 #pragma unroll 8
-      for (int k = 0; k < PB; ++k) {
-        const float4 av = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
-        const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
-        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+        for (int k = 0; k < PB; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(Vt + (k0 + k) * kWLd + 4 * rg);
+          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a4[i], b4[jj], acc[i][jj]);
+        }
+      } else {
+        // diagonal block: x := (x - acc) Linv^T; the rows are this warp's own
+        const int kmax = min(PB, r - c0);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int c = c0 + 4 * cg + jj;
+          if (c < r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][jj];
+        }
+        __syncwarp();
+        float x[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(a4[i], b4[jj], acc[i][jj]);
+          for (int jj = 0; jj < 4; ++jj) x[i][jj] = 0.f;
+        for (int k = 0; k < kmax; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
+          const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
+          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) x[i][jj] = fmaf(a4[i], b4[jj], x[i][jj]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int c = c0 + 4 * cg + jj;
+          if (c < r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][jj];
+        }
+        __syncwarp();
       }
-    } else {
-      // diagonal block: x := (x - acc) Linv^T; the rows are this warp's own
-      const int kmax = min(PB, r - c0);
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int c = c0 + 4 * cg + jj;
-        if (c < r)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] -= acc[i][jj];
-      }
-      __syncwarp();
-      float x[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) x[i][jj] = 0.f;
-      for (int k = 0; k < kmax; ++k) {
-        const float4 av = *reinterpret_cast<const float4*>(Vt + (c0 + k) * kWLd + 4 * rg);
-        const float4 bv = *reinterpret_cast<const float4*>(buf + k * kTLd + 4 * cg);
-        const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) x[i][jj] = fmaf(a4[i], b4[jj], x[i][jj]);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int c = c0 + 4 * cg + jj;
-        if (c < r)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) Vt[c * kWLd + 4 * rg + i] = x[i][jj];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.f;
+      bsel ^= 1;
     }
-    bsel ^= 1;
-    if (++j > cb) { ++cb; j = 0; }
-  };
-  const int ntiles = nb * (nb + 1) / 2;
-  for (int q = 0; q < ntiles; q += 4) {
-    step(pre0, pre3);
-    if (q + 1 < ntiles) step(pre1, pre0);
-    if (q + 2 < ntiles) step(pre2, pre1);
-    if (q + 3 < ntiles) step(pre3, pre2);
   }
   __syncthreads();
   if ((s & 3) == 0 && row0 + kWRows <= s && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
