@@ -602,29 +602,21 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
       while (kmin <= p) kmin += kCL;
       if (kmin < nb) {
         // panel p, rows g_lo .. rp-1: the owner uses its own copy, the
-        // others copy it from the owner's shared memory (distributed shared
-        // memory, same row layout; final since the owner factored it before
-        // the last cluster barrier, and never written again in this attempt)
+        // others read it from L (column-major, written before the barrier)
         const int owner = p % kCL, g_lo = PB * kmin;
         const float* P;
-        const float* own = store + (dsm_slot_offset(owner, p / kCL, rp) + (g_lo - PB * p)) * LD;
         if (owner == rank) {
-          P = own;
+          P = store + (dsm_slot_offset(rank, p / kCL, rp) + (g_lo - PB * p)) * LD;
         } else {
-          const int n = (rp - g_lo) * PB;
-          const float* R = cluster.map_shared_rank(const_cast<float*>(own), owner);
-          for (int e0 = t; e0 < n; e0 += 4 * kChol) {
-            float v[4];
+          const int nrows = rp - g_lo;
+          const float* Lp = Lout + (int64_t)r * (PB * p) + g_lo;
+          for (int i = t; i < nrows; i += kChol) {
+            const bool in = g_lo + i < r;
+            float v[PB];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int e = e0 + u * kChol;
-              v[u] = e < n ? R[(e >> 5) * LD + (e & 31)] : 0.f;
-            }
+            for (int c = 0; c < PB; ++c) v[c] = in ? __ldcg(Lp + i + (int64_t)r * c) : 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int e = e0 + u * kChol;
-              if (e < n) Pl_alloc[(e >> 5) * LD + (e & 31)] = v[u];
-            }
+            for (int c = 0; c < PB; ++c) Pl_alloc[i * LD + c] = v[c];
           }
           P = Pl_alloc;
         }
