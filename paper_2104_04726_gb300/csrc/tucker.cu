@@ -36,9 +36,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
-#include <string>
-#include <unordered_map>
 
 #include "gemm.cuh"
 #include "gemm_tc.cuh"
@@ -264,11 +261,26 @@ struct Driver {
 
 // Reconstruction T_hat = Q x_1 S1 x_2 S2 x_{n>=3} S_n (Eq. 1): the small
 // modes by fibre mixing, then mode 2, then mode 1 with an optional fused
-// residual against `ref`.
+// residual against `ref`.  Every workspace request comes before the first
+// launch, so with a dry Scratch the call only counts bytes (no pointer is
+// read).
 mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float* const* fac, float* out,
                                 const float* ref, double* sse, mes::Scratch& scr, float* T1, float* T2,
                                 float* Kmat, cudaStream_t st, int prec = MES_PREC_FP32, int* err = nullptr) {
   const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
+  auto small_modes = [&](float* dst) -> mes_status {   // T1[q2 + r2 q1 + r1 r2 l] = Q x_{n>=3} S_n
+    KronDesc kd;
+    kd.nm = sh.nsm;
+    for (int m = 0; m < sh.nsm; ++m) {
+      kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'N'; kd.U[m] = fac[m + 2];
+    }
+    MES_TRY(mes::kron_build(kd, Kmat, nullptr, st));
+    Fibres fb;
+    fb.F_lo = r1; fb.F_hi = r2;
+    fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
+    fb.out = dst; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
+    return mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st);
+  };
   if (prec != MES_PREC_FP32 && r1 % 4 == 0 && r2 % 4 == 0) {
     // tensor-core form: the same two products with K-major operands (the
     // factors transposed to rank-fastest copies), every operand split into
@@ -286,22 +298,6 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
     MES_TRY(scr.alloc(&T1l, r1 * r2 * L));
     MES_TRY(scr.alloc(&T2h, r1 * s2 * L));
     MES_TRY(scr.alloc(&T2l, r1 * s2 * L));
-    MES_TRY(mes::slice_transpose(fac[0], s1, r1, 1, U0t, nullptr, 64, st));
-    MES_TRY(mes::slice_transpose(fac[1], s2, r2, 1, U1t, nullptr, 64, st));
-    MES_TRY(mes::split_tf32(U0t, U0h, U0l, s1 * r1, st));
-    MES_TRY(mes::split_tf32(U1t, U1h, U1l, s2 * r2, st));
-    KronDesc kd;
-    kd.nm = sh.nsm;
-    for (int m = 0; m < sh.nsm; ++m) {
-      kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'N'; kd.U[m] = fac[m + 2];
-    }
-    MES_TRY(mes::kron_build(kd, Kmat, nullptr, st));
-    Fibres fb;
-    fb.F_lo = r1; fb.F_hi = r2;
-    fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
-    fb.out = T1; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
-    MES_TRY(mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st));
-    MES_TRY(mes::split_tf32(T1, T1h, T1l, r1 * r2 * L, st));
     Gemm g = Gemm();   // T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2t[q2 + r2 y]
     g.M = r1; g.N = s2; g.K_lo = r2; g.batch = (int)L;
     g.A = T1h; g.A2 = T1l; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
@@ -313,13 +309,20 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
     h.B = T2h; h.B2 = T2l; h.b_n = r1; h.b_k = 1;
     h.C = out; h.c_m = 1; h.c_n = s1;
     if (mes::tc_eligible(g, 2) && mes::tc_eligible(h, 2)) {
+      double* part = nullptr;
+      const int64_t np = mes::gemm_partials(h) * 2 + 16;   // TC tiles are 128 x 128 or 128 x 256
+      if (ref && sse) MES_TRY(scr.alloc(&part, np));
+      if (scr.dry) return MES_OK;
+      MES_TRY(mes::slice_transpose(fac[0], s1, r1, 1, U0t, nullptr, 64, st));
+      MES_TRY(mes::slice_transpose(fac[1], s2, r2, 1, U1t, nullptr, 64, st));
+      MES_TRY(mes::split_tf32(U0t, U0h, U0l, s1 * r1, st));
+      MES_TRY(mes::split_tf32(U1t, U1h, U1l, s2 * r2, st));
+      MES_TRY(small_modes(T1));
+      MES_TRY(mes::split_tf32(T1, T1h, T1l, r1 * r2 * L, st));
       MES_TRY(mes::gemm_tc(g, 2, nullptr, 0, err, st));
       MES_TRY(mes::split_tf32(T2, T2h, T2l, r1 * s2 * L, st));
       if (ref && sse) {
         // one pass stores the product (when out is given) and accumulates the residual
-        double* part = nullptr;
-        const int64_t np = mes::gemm_partials(h) * 2 + 16;   // TC tiles are 128 x 128 or 128 x 256
-        MES_TRY(scr.alloc(&part, np));
         MES_CUDA_TRY(cudaMemsetAsync(part, 0, np * sizeof(double), st));
         h.ref = ref;
         h.partials = part;
@@ -331,36 +334,28 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
       return MES_OK;
     }
   }
-  // T1[q2 + r2 q1 + r1 r2 l] = (Q x_{n>=3} S_n)
-  KronDesc kd;
-  kd.nm = sh.nsm;
-  for (int m = 0; m < sh.nsm; ++m) {
-    kd.s[m] = (int)sh.s[m + 2]; kd.r[m] = (int)sh.r[m + 2]; kd.op[m] = 'N'; kd.U[m] = fac[m + 2];
-  }
-  MES_TRY(mes::kron_build(kd, Kmat, nullptr, st));
-  Fibres fb;
-  fb.F_lo = r1; fb.F_hi = r2;
-  fb.in = core; fb.in_lo = 1; fb.in_hi = r1; fb.in_l = r1 * r2;
-  fb.out = T1; fb.out_lo = r2; fb.out_hi = 1; fb.out_l = r1 * r2;
-  MES_TRY(mes::mix_fibres(fb, Kmat, (int)Lr, (int)L, nullptr, st));
-  // T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2[y + s2 q2]
+  // CUDA-core form.  T2[q1 + r1 y + r1 s2 l] = sum_q2 T1[q2 + r2 q1 + r1 r2 l] S2[y + s2 q2]
   Gemm g = Gemm();
   g.M = r1; g.N = s2; g.K_lo = r2; g.batch = (int)L;
   g.A = T1; g.a_m = r2; g.a_k = 1; g.a_b = r1 * r2;
-  g.B = fac[1]; g.b_n = 1; g.b_k = s2; g.b_b = 0;
+  g.b_n = 1; g.b_k = s2; g.b_b = 0;
   g.C = T2; g.c_m = 1; g.c_n = r1; g.c_b = r1 * s2;
-  MES_TRY(mes::gemm_f32(g, st));
   // out[x + s1 n] = sum_q1 S1[x + s1 q1] T2[q1 + r1 n],  n = y + s2 l
   Gemm h = Gemm();
   h.M = s1; h.N = s2 * L; h.K_lo = r1;
-  h.A = fac[0]; h.a_m = 1; h.a_k = s1;
+  h.a_m = 1; h.a_k = s1;
   h.B = T2; h.b_n = r1; h.b_k = 1;
   h.C = out; h.c_m = 1; h.c_n = s1;
+  double* part = nullptr;
+  const int64_t np = mes::gemm_partials(h);
+  if (ref && sse) MES_TRY(scr.alloc(&part, np));
+  if (scr.dry) return MES_OK;
+  g.B = fac[1];
+  h.A = fac[0];
+  MES_TRY(small_modes(T1));
+  MES_TRY(mes::gemm_f32(g, st));
   if (ref && sse) {
     // one pass stores the product (when out is given) and accumulates the residual
-    double* part = nullptr;
-    const int64_t np = mes::gemm_partials(h);
-    MES_TRY(scr.alloc(&part, np));
     h.ref = ref;
     h.partials = part;
     MES_TRY(mes::gemm_f32(h, st));
@@ -499,6 +494,11 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   MES_TRY(scr.alloc(&order, rmax));
   d.flags = flags;
   if (ws_bytes) {
+    // the fit's reconstruction with fused residual draws from the same
+    // workspace (counted, nothing enqueued: the Scratch is dry)
+    // (T1 stands in for the reference tensor: any non-null pointer, unread)
+    MES_TRY(mes_reconstruct_impl(sh, core, factors, nullptr, T1, sse, scr, T1, T2, d.Kmat, st,
+                                 tf32 ? MES_PREC_TF32 : MES_PREC_FP32, flags));
     *ws_bytes = scr.total;
     return MES_OK;
   }
@@ -929,160 +929,11 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
                               precision == MES_PREC_FP32 ? MES_PREC_FP32 : MES_PREC_TF32, err);
 }
 
-// ---- replay of repeated calls ----
-// A decomposition enqueues about 1100 launches from the host (1920x1080x3x10,
-// 20 sweeps), which with many streams in flight costs as much as the GPU
-// work.  A call repeated with identical arguments -- every pointer, size and
-// option, the stream and the device -- is captured once, on its second
-// occurrence, into a CUDA graph (its stream-ordered workspace becomes graph
-// memory nodes) and replayed from then on: the same kernels with the same
-// launch shapes, so the results are bit-identical to the eager call.  Only
-// on a stream that can be captured (not the legacy or per-thread default
-// stream, not already capturing), with the kernel profiler and the tile
-// tuner off; MES_GRAPH=0 turns it off.  One-off calls (the serving loop,
-// fresh buffers every call) never get past the first occurrence.
-namespace {
-
-struct Replay {
-  int seen = 0;
-  cudaGraphExec_t exec = nullptr;
-  uint64_t used = 0;
-};
-std::mutex g_replay_mu;
-std::unordered_map<std::string, Replay> g_replay;
-uint64_t g_replay_clock = 0;
-constexpr size_t kReplayKeys = 256;   // remembered argument sets
-constexpr int kReplayGraphs = 8;      // instantiated graphs kept
-
-bool replay_enabled(cudaStream_t st) {
-  static int env = -1;
-  if (env < 0) {
-    const char* e = getenv("MES_GRAPH");
-    env = (e && e[0] == '0') ? 0 : 1;
-  }
-  if (!env || mes::prof_on() || getenv("MES_DEBUG")) return false;
-  const char* t = getenv("MES_TUNE");
-  if (t && t[0] == '1') return false;
-  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return false;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return cs == cudaStreamCaptureStatusNone;
-}
-
-template <class T>
-void put(std::string& k, const T& v) {
-  k.append(reinterpret_cast<const char*>(&v), sizeof(T));
-}
-
-std::string replay_key(const float* X, int N, const int64_t* dims, const int64_t* ranks, int max_iters, double tol,
-                       float* core, float* const* factors, double* fit, const mes_als_opts* opts, cudaStream_t st) {
-  std::string k;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  put(k, dev); put(k, st); put(k, X); put(k, N); put(k, max_iters); put(k, tol); put(k, core); put(k, fit);
-  for (int n = 0; n < N; ++n) { put(k, dims[n]); put(k, ranks[n]); put(k, factors[n]); }
-  mes_als_opts o;
-  memset(&o, 0, sizeof(o));
-  if (opts) o = *opts;
-  put(k, o.precision); put(k, o.init_iters); put(k, o.inner_iters); put(k, o.seed); put(k, o.iters_done);
-  put(k, o.fit_history); put(k, o.canonical); put(k, o.init);
-  const bool given = o.init_factors != nullptr;
-  put(k, given);
-  if (given)
-    for (int n = 0; n < N; ++n) put(k, o.init_factors[n]);
-  return k;
-}
-
-// drop the least recently used entries beyond the limits (caller holds the lock)
-void replay_trim() {
-  while (g_replay.size() > kReplayKeys) {
-    auto old = g_replay.begin();
-    for (auto it = g_replay.begin(); it != g_replay.end(); ++it)
-      if (it->second.used < old->second.used) old = it;
-    if (old->second.exec) cudaGraphExecDestroy(old->second.exec);   // freed after any launch in flight
-    g_replay.erase(old);
-  }
-  int graphs = 0;
-  for (auto& kv : g_replay) graphs += kv.second.exec != nullptr;
-  while (graphs > kReplayGraphs) {
-    Replay* old = nullptr;
-    for (auto& kv : g_replay)
-      if (kv.second.exec && (!old || kv.second.used < old->used)) old = &kv.second;
-    cudaGraphExecDestroy(old->exec);
-    old->exec = nullptr;
-    old->seen = 0;
-    --graphs;
-  }
-}
-
-}  // namespace
-
 extern "C" mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
                                      int max_iters, double tol, float* core, float* const* factors,
                                      double* fit, const mes_als_opts* opts, void* stream) {
   mes::clear_error();
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the arguments must be readable to form the key; anything invalid goes
-  // to the eager path, which reports it
-  const bool keyable = dims && ranks && factors && N >= 2 && N <= 8;
-  if (!keyable || !replay_enabled(st))
-    return tucker_als_impl(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, stream, nullptr);
-  const std::string key = replay_key(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, st);
-  cudaGraphExec_t exec = nullptr;
-  bool capture = false;
-  {
-    std::lock_guard<std::mutex> lk(g_replay_mu);
-    auto it = g_replay.find(key);
-    if (it != g_replay.end()) {
-      it->second.used = ++g_replay_clock;
-      exec = it->second.exec;
-      capture = !exec && it->second.seen >= 1;
-    }
-  }
-  if (exec) {
-    MES_CUDA_TRY(cudaGraphLaunch(exec, st));
-    return MES_OK;
-  }
-  if (capture) {
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-      const mes_status s = tucker_als_impl(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, stream,
-                                           nullptr);
-      const cudaError_t e = cudaStreamEndCapture(st, &graph);
-      cudaGraphExec_t made = nullptr;
-      if (s == MES_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&made, graph, 0) == cudaSuccess) {
-        cudaGraphDestroy(graph);
-        {
-          std::lock_guard<std::mutex> lk(g_replay_mu);
-          Replay& r = g_replay[key];
-          if (r.exec) cudaGraphExecDestroy(r.exec);
-          r.exec = made;
-          r.used = ++g_replay_clock;
-          replay_trim();
-        }
-        MES_CUDA_TRY(cudaGraphLaunch(made, st));
-        return MES_OK;
-      }
-      if (graph) cudaGraphDestroy(graph);
-    }
-    // capture failed: nothing was enqueued; stop trying for this key and run eagerly
-    cudaGetLastError();
-    mes::clear_error();
-    std::lock_guard<std::mutex> lk(g_replay_mu);
-    g_replay[key].seen = -1000000;
-  }
-  const mes_status s = tucker_als_impl(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, stream, nullptr);
-  if (s == MES_OK) {
-    std::lock_guard<std::mutex> lk(g_replay_mu);
-    Replay& r = g_replay[key];
-    ++r.seen;
-    r.used = ++g_replay_clock;
-    replay_trim();
-  }
-  return s;
+  return tucker_als_impl(X, N, dims, ranks, max_iters, tol, core, factors, fit, opts, stream, nullptr);
 }
 
 extern "C" mes_status mes_tucker_als_workspace_size(int N, const int64_t* dims, const int64_t* ranks,
