@@ -170,7 +170,8 @@ def cpu_baseline(sample_sweeps: int = 1):
 def _config(name, cfg, dims, ranks, precision, stacks, world):
     return {"workload": name, "dims": dims, "ranks": ranks, "sweeps": cfg["iters"], "colour": cfg["space"],
             "precision": precision, "quant_bits": 16, "stacks_per_step": stacks,
-            "l2": "inputs larger than L2 (each stack: 249 MB FP32 tensor + 249 MB second layout)",
+            "l2": "inputs larger than L2: each stack's tensor is 249 MB in FP32 (124 MB per BF16 layout), "
+                  "read twice per sweep",
             "parallelism": f"stack-parallel x{world}"}
 
 
