@@ -419,9 +419,7 @@ mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, d
  * C[b][m][n] = sum_k A[b][m][k] * B[b][n][k], all row-major FP32 device
  * arrays, batch >= 1.  impl 0: CUDA-core FP32 kernel; 1: tcgen05 kind::tf32;
  * 2: tcgen05 kind::f16 on BF16-rounded copies of A and B; 3: tcgen05
- * kind::tf32 on the three-term split (hi + lo of A and B); 4: as 2 with both
- * copies in the tile-blocked layout (128 x 64 tiles, one contiguous block
- * each; K a multiple of 8).  Synchronises the
+ * kind::tf32 on the three-term split (hi + lo of A and B).  Synchronises the
  * stream.  MES_ERR_INVALID_ARG for bad sizes or operands the tensor-core
  * kernel cannot address (row strides must be multiples of 16 bytes);
  * MES_ERR_TIMEOUT if a bounded pipeline wait gave up.

@@ -47,10 +47,6 @@ struct Gemm {
   // summed in a fixed order).  Used when the tile grid leaves most SMs idle.
   float* split_ws = nullptr;
   int64_t split_elems = 0;
-  // Tensor-core BF16 products only (K_hi == 1): the operand is stored in the
-  // tile-blocked layout of block16 (rows M or N, K, batch when batched); its
-  // row, K and batch strides above are then not used.
-  bool a_blocked = false, b_blocked = false;
 };
 
 // FP32 CUDA-core path.

@@ -46,7 +46,6 @@ struct TcArgs {
   int64_t M, N;
   int k_tiles_lo, k_tiles_total, kt_per_split, splits, batch;
   int a_batched, b_batched;   // 0: operand shared by all batches (coordinate 0)
-  int a_blocked, b_blocked;   // operand in the tile-blocked layout (5-D map)
   float* C;
   int64_t M_lo, c_m, c_mh, N_lo, c_n, c_nh, c_b;
   float* C2;
@@ -110,17 +109,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
       "[%2];" ::"r"(smem_u32(dst)),
       "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
-// a 128 x 64 tile (or two stacked) of a tile-blocked operand: coordinates
-// {0, 0, k block, row block, batch}
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c2, int c3,
-                                            int c4) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %3, %4, %5, "
-      "%6}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(0), "r"(c2), "r"(c3), "r"(c4)
       : "memory");
 }
 
@@ -281,14 +269,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
       uint8_t* sa = tiles + stage * C::STAGE;
       mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
-      if (args.a_blocked)
-        tma_load_5d(sa, &mapA, &full[stage], kt, (int)(m0 / BM), args.a_batched ? b : 0);
-      else
-        tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
-      if (args.b_blocked)
-        tma_load_5d(sa + C::A_BYTES, &mapB, &full[stage], kt, (int)(n0 / BM), args.b_batched ? b : 0);
-      else
-        tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+      tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
+      tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
       if (KIND == 2) {
         uint8_t* sl = sa + C::A_BYTES + C::B_BYTES;
         tma_load_4d(sl, &mapA2, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
@@ -532,23 +514,6 @@ bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_
   return r == CUDA_SUCCESS;
 }
 
-// 5-D map {64, 128, k blocks, row blocks, batch} of a BF16 operand in the
-// tile-blocked layout (block16): every 128 x 64 tile is one contiguous 16 KB
-// block; a box is box_rows / 128 such blocks of consecutive row blocks.
-bool make_map_blocked(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int64_t batch, int box_rows) {
-  const int64_t KB = (K + 63) / 64, RB = (rows + 127) / 128;
-  cuuint64_t dims[5] = {64, 128, (cuuint64_t)KB, (cuuint64_t)RB, (cuuint64_t)batch};
-  const int64_t tile = 128 * 64 * 2;
-  cuuint64_t strides[4] = {128, (cuuint64_t)tile, (cuuint64_t)(KB * tile), (cuuint64_t)(RB * KB * tile)};
-  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || RB * KB * tile * batch >= ((int64_t)1 << 40)) return false;
-  cuuint32_t box[5] = {64, 128, 1, (cuuint32_t)(box_rows / 128), 1};
-  cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 template <int KIND, int BN, int STAGES>
 mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& ma2, const CUtensorMap& mb2,
                      const TcArgs& a, dim3 grid, bool resid, cudaStream_t st) {
@@ -575,16 +540,6 @@ namespace mes {
 
 bool tc_eligible(const Gemm& g, int kind) {
   const int E = kind == 1 ? 2 : 4;
-  if (g.a_blocked || g.b_blocked) {
-    // tile-blocked operands: BF16 only, K in one piece; the other operand
-    // must satisfy the strided rules below
-    if (kind != 1 || g.K_hi != 1) return false;
-    Gemm h = g;
-    h.a_blocked = h.b_blocked = false;
-    if (g.a_blocked) { h.a_m = 8; h.a_k = 1; h.a_b = g.a_b != 0 ? 8 : 0; }
-    if (g.b_blocked) { h.b_n = 8; h.b_k = 1; h.b_b = g.b_b != 0 ? 8 : 0; }
-    return tc_eligible(h, kind);
-  }
   if (kind == 2 && (!g.A2 || !g.B2 || reinterpret_cast<uintptr_t>(g.A2) % 16 || reinterpret_cast<uintptr_t>(g.B2) % 16))
     return false;
   if (g.a_k != 1 || g.b_k != 1) return false;
@@ -611,13 +566,9 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   if (kind == 2 || (bn != 128 && bn != 256)) bn = 128;   // KIND 2 has only the 128-wide tile
   CUtensorMap ma, mb, ma2, mb2;
   const bool ab = g.batch > 1 && g.a_b != 0, bb = g.batch > 1 && g.b_b != 0;
-  const bool ok_a = g.a_blocked ? make_map_blocked(&ma, g.A, g.M, g.K_lo, ab ? g.batch : 1, BM)
-                                : make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh,
-                                           g.a_b, BM);
-  const bool ok_b = g.b_blocked ? make_map_blocked(&mb, g.B, g.N, g.K_lo, bb ? g.batch : 1, bn)
-                                : make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh,
-                                           g.b_b, bn);
-  if (!ok_a || !ok_b) return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map rejected");
+  if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
+      !make_map(&mb, g.B, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh, g.b_b, bn))
+    return fail(MES_ERR_INVALID_ARG, "gemm_tc: tensor map rejected");
   if (kind == 2) {
     if (!make_map(&ma2, g.A2, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
         !make_map(&mb2, g.B2, kind, g.K_lo, g.N, g.K_hi, bb ? g.batch : 1, g.b_n, g.b_kh, g.b_b, bn))
@@ -634,8 +585,6 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   a.batch = g.batch;
   a.a_batched = ab ? 1 : 0;
   a.b_batched = bb ? 1 : 0;
-  a.a_blocked = g.a_blocked ? 1 : 0;
-  a.b_blocked = g.b_blocked ? 1 : 0;
   a.C = g.C;
   a.M_lo = g.M_lo > 0 ? g.M_lo : g.M;
   a.c_m = g.c_m; a.c_mh = g.c_mh;
@@ -736,9 +685,8 @@ bool tuning_on() {
 
 std::string tune_key(const mes::Gemm& g, int kind) {
   char buf[200];
-  snprintf(buf, sizeof buf, "k%d m%lld n%lld kl%lld kh%lld b%d ab%d bb%d bl%d%d", kind, (long long)g.M,
-           (long long)g.N, (long long)g.K_lo, (long long)g.K_hi, g.batch, g.a_b != 0 ? 1 : 0, g.b_b != 0 ? 1 : 0,
-           g.a_blocked ? 1 : 0, g.b_blocked ? 1 : 0);
+  snprintf(buf, sizeof buf, "k%d m%lld n%lld kl%lld kh%lld b%d ab%d bb%d", kind, (long long)g.M, (long long)g.N,
+           (long long)g.K_lo, (long long)g.K_hi, g.batch, g.a_b != 0 ? 1 : 0, g.b_b != 0 ? 1 : 0);
   return buf;
 }
 
@@ -832,13 +780,12 @@ __global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16_raw* 
 
 // Test hook: C[m*N + n] = sum_k A[m*K + k] * B[n*K + k] (both row-major,
 // K-major), through the CUDA-core kernel (impl 0), kind::tf32 (impl 1),
-// kind::f16 on BF16-rounded inputs (impl 2), the three-term TF32 split of
-// A and B (impl 3), or kind::f16 on BF16-rounded inputs copied to the
-// tile-blocked layout (impl 4; K a multiple of 8).
+// kind::f16 on BF16-rounded inputs (impl 2) or the three-term TF32 split of
+// A and B (impl 3).
 extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M,
                                         int64_t N, int64_t K, int batch, void* stream) {
   mes::clear_error();
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 4 || (impl == 4 && K % 8))
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 3)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_gemm_selftest: bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
@@ -858,7 +805,7 @@ extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B
   MES_TRY(scr.alloc(&err, 1));
   MES_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   MES_TRY(scr.alloc(&ws, ws_elems));
-  if (impl == 2 || impl == 4) {
+  if (impl == 2) {
     __nv_bfloat16_raw *Ab, *Bb;
     MES_TRY(scr.alloc(&Ab, batch * M * K));
     MES_TRY(scr.alloc(&Bb, batch * N * K));
@@ -867,16 +814,6 @@ extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B
     MES_LAUNCH_CHECK();
     g.A = reinterpret_cast<const float*>(Ab);
     g.B = reinterpret_cast<const float*>(Bb);
-    if (impl == 4) {
-      uint16_t *Ak, *Bk;
-      MES_TRY(scr.alloc(&Ak, mes::block16_elems(M, K, batch)));
-      MES_TRY(scr.alloc(&Bk, mes::block16_elems(N, K, batch)));
-      MES_TRY(mes::block16(reinterpret_cast<const uint16_t*>(Ab), M, K, K, M * K, batch, Ak, st));
-      MES_TRY(mes::block16(reinterpret_cast<const uint16_t*>(Bb), N, K, K, N * K, batch, Bk, st));
-      g.A = reinterpret_cast<const float*>(Ak);
-      g.B = reinterpret_cast<const float*>(Bk);
-      g.a_blocked = g.b_blocked = true;
-    }
   }
   if (impl == 3) {
     float *Ah, *Al, *Bh, *Bl;
@@ -889,7 +826,7 @@ extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B
     g.A = Ah; g.A2 = Al;
     g.B = Bh; g.B2 = Bl;
   }
-  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : impl == 2 || impl == 4 ? 1 : 2, ws, ws_elems, err, st));
+  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : impl == 2 ? 1 : 2, ws, ws_elems, err, st));
   int herr = 0;
   MES_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   MES_CUDA_TRY(cudaStreamSynchronize(st));

@@ -81,25 +81,6 @@ __global__ void split_tf32_kernel(const float* __restrict__ in, float* __restric
   }
 }
 
-// One 128 x 64 tile per block: 1024 chunks of 8 elements (16 bytes), 8 per
-// thread; a chunk outside R or K is zero.
-__global__ void __launch_bounds__(128)
-block16_kernel(const uint16_t* __restrict__ src, int64_t R, int64_t K, int64_t ld, int64_t bstride, int64_t RB,
-               int64_t KB, uint16_t* __restrict__ dst) {
-  const int64_t tile = blockIdx.x;
-  const int64_t kb = tile % KB, rb = (tile / KB) % RB, b = tile / (KB * RB);
-  const uint16_t* s = src + b * bstride;
-  uint4* d = reinterpret_cast<uint4*>(dst + tile * 8192);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = threadIdx.x + q * 128;   // chunk: row c / 8, elements 8 (c % 8) ..
-    const int64_t r = rb * 128 + (c >> 3), k = kb * 64 + (c & 7) * 8;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r < R && k < K) v = __ldg(reinterpret_cast<const uint4*>(s + r * ld + k));
-    d[c] = v;
-  }
-}
-
 __global__ void to_bf16_kernel(const float* __restrict__ in, uint16_t* __restrict__ out, int64_t n,
                                const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -385,25 +366,6 @@ mes_status split_tf32(const float* in, float* hi, float* lo, int64_t n, cudaStre
 mes_status to_bf16(const float* in, uint16_t* out, int64_t n, const int* skip, cudaStream_t st) {
   ProfScope prof("to_bf16", st, 0.0, 6.0 * n);
   to_bf16_kernel<<<grid_for(n, kT, 2048), kT, 0, st>>>(in, out, n, skip);
-  MES_LAUNCH_CHECK();
-  return MES_OK;
-}
-
-int64_t block16_elems(int64_t R, int64_t K, int batch) {
-  return (int64_t)batch * ((R + 127) / 128) * ((K + 63) / 64) * 8192;
-}
-
-mes_status block16(const uint16_t* src, int64_t R, int64_t K, int64_t ld, int64_t bstride, int batch,
-                   uint16_t* dst, cudaStream_t st) {
-  if (K % 8 || ld % 8 || bstride % 8 || (reinterpret_cast<uintptr_t>(src) & 15) ||
-      (reinterpret_cast<uintptr_t>(dst) & 15))
-    return fail(MES_ERR_INVALID_ARG, "block16: K, strides and pointers must be 16-byte multiples");
-  MES_TRY(audit(src, (size_t)(((int64_t)(batch - 1) * bstride + (R - 1) * ld + K) * 2) - 1, "block16 src"));
-  MES_TRY(audit(dst, (size_t)(block16_elems(R, K, batch) * 2) - 1, "block16 dst"));
-  ProfScope prof("block16", st, 0.0, 4.0 * batch * R * K);
-  const int64_t RB = (R + 127) / 128, KB = (K + 63) / 64;
-  const int64_t tiles = (int64_t)batch * RB * KB;
-  block16_kernel<<<(unsigned)tiles, 128, 0, st>>>(src, R, K, ld, bstride, RB, KB, dst);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

@@ -41,18 +41,6 @@ mes_status slice_transpose(const float* X, int64_t s1, int64_t s2, int64_t L, fl
 mes_status split_tf32(const float* in, float* hi, float* lo, int64_t n, cudaStream_t st, const int* skip = nullptr);
 // out = bits of round_bf16(in), elementwise; a no-op when *skip != 0
 mes_status to_bf16(const float* in, uint16_t* out, int64_t n, const int* skip, cudaStream_t st);
-
-// Tile-blocked copy of a BF16 K-major operand for the tensor-core products:
-// rows r < R with K contiguous elements at src + r * ld + b * bstride
-// (ld, bstride in elements, multiples of 8; K a multiple of 8) become
-// 128-row x 64-element tiles, each a contiguous 16 KB block,
-//   dst[((b * RB + r / 128) * KB + k / 64) * 8192 + (r % 128) * 64 + k % 64],
-// RB = ceil(R / 128), KB = ceil(K / 64), zero beyond R and K.  One TMA box of
-// the product then reads one DRAM-contiguous block instead of 128 pieces of
-// 128 bytes that lie a row apart.
-int64_t block16_elems(int64_t R, int64_t K, int batch);
-mes_status block16(const uint16_t* src, int64_t R, int64_t K, int64_t ld, int64_t bstride, int batch,
-                   uint16_t* dst, cudaStream_t st);
 // out = round_tf32(in), elementwise
 mes_status round_copy(const float* in, float* out, int64_t n, const int* skip, cudaStream_t st);
 // out = in, elementwise; a no-op when *skip != 0

@@ -436,10 +436,6 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   const bool bf = precision == MES_PREC_BF16 && s1 % 8 == 0 && s2 % 8 == 0;
   const bool tf32 = precision != MES_PREC_FP32;   // tensor-core forms
   uint16_t *X16 = nullptr, *XB16 = nullptr, *U16[2] = {nullptr, nullptr};
-  // the BF16 copies again in the tile-blocked layout, for the T-side products
-  // of every sweep (P reads XB16b, Ca reads X16b): one TMA box is then one
-  // contiguous 16 KB block of DRAM; the initialisation keeps the plain copies
-  uint16_t *X16b = nullptr, *XB16b = nullptr;
   if (!bf) MES_TRY(scr.alloc(&XB, nel));
   if (tf32) {
     // operands of the kind::tf32 products, pre-rounded to nearest TF32
@@ -450,8 +446,6 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (bf) {
     MES_TRY(scr.alloc(&X16, nel));
     MES_TRY(scr.alloc(&XB16, nel));
-    MES_TRY(scr.alloc(&X16b, mes::block16_elems(s2 * L, s1, 1)));
-    MES_TRY(scr.alloc(&XB16b, mes::block16_elems(s1, s2, (int)L)));
     MES_TRY(scr.alloc(&U16[0], s1 * r1));
     MES_TRY(scr.alloc(&U16[1], s2 * r2));
     MES_TRY(scr.alloc(&d.Zh16, zsz));
@@ -516,11 +510,6 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
 
   // ---- second layout of T and ||T||^2 ----
   MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st, Xr, tf32, X16, XB16));
-  if (bf) {
-    // X16b: rows n = y + s2 l, K = x;  XB16b: per slice l, rows x, K = y
-    MES_TRY(mes::block16(X16, s2 * L, s1, s1, 0, 1, X16b, st));
-    MES_TRY(mes::block16(XB16, s1, s2, s2, s1 * s2, (int)L, XB16b, st));
-  }
   const float* Xop = tf32 ? Xr : X;    // T as an operand of the large products
   MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
 
@@ -585,8 +574,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     g.C2 = Cat; g.c2_m = s2; g.c2_n = 1; g.c2_nh = s2 * r1;
     if (!use16) return d.big(g);
     g.A = reinterpret_cast<const float*>(U16[0]);
-    g.B = reinterpret_cast<const float*>(X16b);
-    g.b_blocked = true;
+    g.B = reinterpret_cast<const float*>(X16);
     return d.big16(g);
   };
   // B = Ca x_2 S2^T: B[(q1 + r1 l) + r1 L q2] = sum_y Cat[y + s2 (q1 + r1 l)] U1[y + s2 q2]
@@ -711,8 +699,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       // second layout Pt[x + s1 (q2 + r2 l)]: the K-major operand of Z below
       g.C2 = Pt; g.c2_m = 1; g.c2_n = s1; g.c2_b = s1 * r2;
       if (bf) {
-        g.A = reinterpret_cast<const float*>(XB16b);
-        g.a_blocked = true;
+        g.A = reinterpret_cast<const float*>(XB16);
         g.B = reinterpret_cast<const float*>(U16[1]);
         MES_TRY(d.big16(g));
       } else {
