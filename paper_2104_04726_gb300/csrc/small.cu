@@ -155,6 +155,35 @@ mix_kernel(mes::Fibres fb, const float* __restrict__ Kmat, int L, int L2, const 
   }
 }
 
+// The same mixing with the fibre held in registers: L <= LMAX (the
+// workloads have L = 3 x 6 .. 3 x 14), loops unrolled and predicated, the
+// products summed in the same order as above, so the results are identical.
+template <int LMAX>
+__global__ void __launch_bounds__(kT)
+mix_reg_kernel(mes::Fibres fb, const float* __restrict__ Kmat, int L, int L2, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ float Ks[];
+  for (int e = threadIdx.x; e < L * L2; e += kT) Ks[e] = Kmat[e];
+  __syncthreads();
+  const int64_t F = fb.F_lo * fb.F_hi;
+  for (int64_t f = (int64_t)blockIdx.x * kT + threadIdx.x; f < F; f += (int64_t)gridDim.x * kT) {
+    const int64_t fh = f / fb.F_lo, fl = f - fh * fb.F_lo;
+    const float* src = fb.in + fl * fb.in_lo + fh * fb.in_hi;
+    float* dst = fb.out + fl * fb.out_lo + fh * fb.out_hi;
+    float v[LMAX];
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) v[l] = l < L ? src[(int64_t)l * fb.in_l] : 0.f;
+    for (int o = 0; o < L2; ++o) {
+      const float* kr = Ks + (int64_t)o * L;
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l)
+        if (l < L) acc = fmaf(kr[l], v[l], acc);
+      dst[(int64_t)o * fb.out_l] = acc;
+    }
+  }
+}
+
 // Gram of one small mode over all fibres.  The fibre is first projected by
 // the L2 x L matrix K (the other small modes' factors, identity on mode n),
 // giving an s_n x (L2/s_n) block with the mode-n index at stride `inner`
@@ -399,6 +428,8 @@ mes_status mix_fibres(const Fibres& fb, const float* Kmat, int L, int L2, const 
   static bool attr = false;
   if (!attr) {
     MES_CUDA_TRY(cudaFuncSetAttribute(mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    MES_CUDA_TRY(cudaFuncSetAttribute(mix_reg_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    MES_CUDA_TRY(cudaFuncSetAttribute(mix_reg_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     attr = true;
   }
   int64_t F = fb.F_lo * fb.F_hi;
@@ -408,7 +439,13 @@ mes_status mix_fibres(const Fibres& fb, const float* Kmat, int L, int L2, const 
                 "mix out"));
   MES_TRY(audit(Kmat, (size_t)L * L2 * 4 - 1, "mix K"));
   ProfScope prof("mix_fibres", st, 2.0 * F * L * L2, 4.0 * F * (L + L2));
-  mix_kernel<<<grid_for(F, kT, (int64_t)sm_count() * 8), kT, smem, st>>>(fb, Kmat, L, L2, skip);
+  const unsigned grid = grid_for(F, kT, (int64_t)sm_count() * 8);
+  if (L <= 32)
+    mix_reg_kernel<32><<<grid, kT, smem, st>>>(fb, Kmat, L, L2, skip);
+  else if (L <= 64)
+    mix_reg_kernel<64><<<grid, kT, smem, st>>>(fb, Kmat, L, L2, skip);
+  else
+    mix_kernel<<<grid, kT, smem, st>>>(fb, Kmat, L, L2, skip);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
