@@ -162,8 +162,13 @@ template <int LMAX>
 __global__ void __launch_bounds__(kT)
 mix_reg_kernel(mes::Fibres fb, const float* __restrict__ Kmat, int L, int L2, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  extern __shared__ float Ks[];
-  for (int e = threadIdx.x; e < L * L2; e += kT) Ks[e] = Kmat[e];
+  extern __shared__ __align__(16) float Ks[];
+  // rows of K padded to a multiple of 4 (zeros) and read as float4
+  const int LP = (L + 3) & ~3;
+  for (int e = threadIdx.x; e < LP * L2; e += kT) {
+    const int o = e / LP, l = e - o * LP;
+    Ks[e] = l < L ? Kmat[o * L + l] : 0.f;
+  }
   __syncthreads();
   const int64_t F = fb.F_lo * fb.F_hi;
   for (int64_t f = (int64_t)blockIdx.x * kT + threadIdx.x; f < F; f += (int64_t)gridDim.x * kT) {
@@ -174,11 +179,19 @@ mix_reg_kernel(mes::Fibres fb, const float* __restrict__ Kmat, int L, int L2, co
 #pragma unroll
     for (int l = 0; l < LMAX; ++l) v[l] = l < L ? src[(int64_t)l * fb.in_l] : 0.f;
     for (int o = 0; o < L2; ++o) {
-      const float* kr = Ks + (int64_t)o * L;
+      const float4* kr = reinterpret_cast<const float4*>(Ks + o * LP);
       float acc = 0.f;
 #pragma unroll
-      for (int l = 0; l < LMAX; ++l)
-        if (l < L) acc = fmaf(kr[l], v[l], acc);
+      for (int l4 = 0; l4 < LMAX / 4; ++l4) {
+        if (4 * l4 < L) {
+          const float4 k = kr[l4];
+          // the same order as the generic kernel: l ascending, l < L only
+          acc = fmaf(k.x, v[4 * l4], acc);
+          if (4 * l4 + 1 < L) acc = fmaf(k.y, v[4 * l4 + 1], acc);
+          if (4 * l4 + 2 < L) acc = fmaf(k.z, v[4 * l4 + 2], acc);
+          if (4 * l4 + 3 < L) acc = fmaf(k.w, v[4 * l4 + 3], acc);
+        }
+      }
       dst[(int64_t)o * fb.out_l] = acc;
     }
   }
@@ -423,7 +436,7 @@ mes_status uniform_fill(float* out, int64_t n, uint64_t seed, cudaStream_t st) {
 
 mes_status mix_fibres(const Fibres& fb, const float* Kmat, int L, int L2, const int* skip,
                       cudaStream_t st) {
-  size_t smem = (size_t)L * L2 * sizeof(float);
+  size_t smem = (size_t)((L + 3) & ~3) * L2 * sizeof(float);   // rows padded for the register kernels
   if (smem > 64 * 1024) return fail(MES_ERR_NOT_IMPLEMENTED, "small modes too large for fibre mixing");
   static bool attr = false;
   if (!attr) {
