@@ -598,7 +598,6 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     bool failed = false;
     for (int p = 0; p < nb - 1; ++p) {
       if (bad0[2 * attempt + ((p - 1) & 1)]) { failed = true; break; }
-      bool arrived = false;
       int kmin = rank;
       while (kmin <= p) kmin += kCL;
       if (kmin < nb) {
@@ -654,20 +653,13 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
           __syncthreads();
           publish(Sk, kmin);
           if (t == 0 && lbad) bad0[2 * attempt + (p & 1)] = 1;
-          // the next panel and its pivot report are out: arrive now, so the
-          // cluster's next step need not wait for this CTA's other columns
-          // (only this CTA reads or writes them before its own wait below)
-          asm volatile("barrier.cluster.arrive.release;" ::: "memory");
-          arrived = true;
           off += h;
           kmin += kCL;
         }
         for (int k = kmin; k < nb; off += rp - PB * k, k += kCL)
           update_col(store + off * LD, k, P, g_lo, 0, rp - PB * k, 0, kChol / 32);
       }
-      // one arrival and one wait per thread and step in every CTA
-      if (!arrived) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
-      asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+      cluster.sync();
     }
     if (!failed && nb >= 2 && bad0[2 * attempt + ((nb - 2) & 1)]) failed = true;
     if (!failed) break;
