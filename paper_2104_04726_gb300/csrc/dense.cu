@@ -431,17 +431,19 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 }
 
 // --------------------------------------------------------------------------
-// chol_dsm: the factorization for 128 < r <= 512 with the whole matrix in the
-// shared memory of a cluster of kCL CTAs, so no phase goes through L2.
+// chol_dsm: the factorization for 128 < r <= 512 with the whole matrix held
+// in the shared memory of a cluster of kCL CTAs.
 // Block column k (rows 32k .. rp-1, rp = r rounded up to 32; rows at and
 // beyond r are zero) lives in CTA k mod kCL, row-major with stride 33.
-// Step p: every CTA that owns a column right of p copies the rows of panel
-// p it needs from the owner's shared memory (distributed shared memory); the
-// owner of column p + 1 applies panel p to that column first, factors its
-// diagonal block in registers and solves its panel (look-ahead), then every
-// CTA applies panel p to the rest of its columns.  One cluster barrier per
-// step; a bad pivot is reported to CTA 0's flag for the attempt and every
-// CTA reads it after the same barrier, so all restart together.
+// Each column is written to L as soon as it is factored; in step p every CTA
+// that owns a column right of p copies the rows of panel p it needs from L
+// (through L2: measured faster here than reading the owner's shared memory
+// across the cluster); the owner of column p + 1 applies panel p to that
+// column first, factors its diagonal block in registers and solves its
+// panel (look-ahead), then every CTA applies panel p to the rest of its
+// columns.  One cluster barrier per step; a bad pivot is reported to CTA 0's
+// flag for the attempt and every CTA reads it after the same barrier, so all
+// restart together.
 // --------------------------------------------------------------------------
 constexpr int kDsmMaxR = 512;
 static_assert(kChol == 256, "the diagonal-block update maps 8 warps to 32 columns");
