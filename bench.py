@@ -523,6 +523,7 @@ def main():
             self.core = torch.empty(mes.torch_shape(ranks), dtype=torch.float32, device=dev)
             self.facs = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
             self.fit = torch.empty((), dtype=torch.float64, device=dev)
+            self.Xh = torch.empty_like(self.X)
             self.itd = torch.zeros((), dtype=torch.int32, device=dev)
             self.stream = torch.cuda.Stream(device=dev)
             self.q_host = torch.empty(mes.torch_shape(ranks), dtype=torch.int16, pin_memory=True)
@@ -535,10 +536,10 @@ def main():
                 if e2e:
                     self.rgb.copy_(self.rgb_host, non_blocking=True)
                 mes.colour_convert(self.rgb, cfg["space"], out=self.X, norm2=self.n2)
+                # the fit's reconstruction pass (fused residual) also stores T_hat
                 mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=precision,
-                               outputs=(self.core, self.facs, self.fit, self.itd, None))
+                               outputs=(self.core, self.facs, self.fit, self.itd, None), reconstruction=self.Xh)
                 q, sc = mes.quantize_core(self.core, ranks, 16)
-                mes.reconstruct(self.core, self.facs, dims, ranks, ref=self.X, precision=precision)
                 if e2e:
                     self.q_host.copy_(q, non_blocking=True)
                     self.s_host.copy_(sc, non_blocking=True)

@@ -159,6 +159,11 @@ typedef struct mes_als_opts {
                            decreasing eigenvalue, sign-fixed; -1 = off        */
   int init;             /* mes_init of the start when init_factors is null
                            (MES_INIT_THOSVD)                                  */
+  float* reconstruction; /* nullable device FP32 tensor of dims `dims`: receives
+                           T_hat = Q x_1 S^(1) ... x_N S^(N) (Eq. 1) of the
+                           returned decomposition, from the same pass that
+                           measures the fit (as mes_reconstruct gives with
+                           precision FP32 for the FP32 form, TF32 otherwise) */
 } mes_als_opts;
 
 /*

@@ -117,14 +117,15 @@ def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=N
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
                precision: str = "fp32", init_iters: int = 0, inner_iters: int = 0, seed: int = 0,
                canonical: bool = True, init_factors=None, history: bool = False, outputs=None,
-               init: str = "thosvd"):
+               init: str = "thosvd", reconstruction=None):
     """Tucker-ALS / HOOI (Section III-B).  X: float32 CUDA tensor holding the
     first-mode-fastest tensor of paper dims `dims`.  Returns a dict with
     `core` (torch shape reversed(ranks)), `factors` (list of (r_n, s_n)
     tensors = column-major S^(n)), `fit` (float64 CUDA scalar), `iters`
     (int32 CUDA scalar) and, if history, `fit_history` (max_iters float64).
     init: "thosvd" (truncated HOSVD) or "interlaced" (interlaced HOSVD); a
-    given `init_factors` overrides both."""
+    given `init_factors` overrides both.  reconstruction: optional float32
+    CUDA tensor like X that receives T_hat (Eq. 1) from the fit's pass."""
     torch = _torch()
     _need(X, torch.float32, "X")
     dims = [int(d) for d in dims]
@@ -154,6 +155,11 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     opts.seed = int(seed)
     opts.canonical = 0 if canonical else -1
     opts.init = INITS[init]
+    if reconstruction is not None:
+        _need(reconstruction, torch.float32, "reconstruction")
+        if reconstruction.numel() != n_el:
+            raise ValueError("reconstruction does not hold prod(dims) elements")
+        opts.reconstruction = reconstruction.data_ptr()
     opts.iters_done = iters.data_ptr()
     opts.fit_history = hist.data_ptr() if hist is not None else None
     keep = None

@@ -72,6 +72,7 @@ class MesAlsOpts(ctypes.Structure):
         ("fit_history", ctypes.c_void_p),
         ("canonical", ctypes.c_int),
         ("init", ctypes.c_int),
+        ("reconstruction", ctypes.c_void_p),
     ]
 
 

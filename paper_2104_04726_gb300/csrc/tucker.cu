@@ -406,6 +406,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     mes::audit_register(X, (size_t)nX * 4);
     mes::audit_register(core, (size_t)nQ * 4);
     for (int n = 0; n < N; ++n) mes::audit_register(factors[n], (size_t)(sh.s[n] * sh.r[n]) * 4);
+    if (o.reconstruction) mes::audit_register(o.reconstruction, (size_t)nX * 4);
   }
   mes::Scratch scr(st, ws_bytes != nullptr);
   Driver d;
@@ -879,17 +880,17 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     fprintf(stderr, "[mes] done=%d numerics_flags=%d chol_calls=%d chol_restarts=%d\n", hf[0], hf[1], hf[2],
             hf[3]);
   }
-  // ---- fit from the explicit residual ----
-  if (fit) {
+  // ---- fit from the explicit residual (and T_hat when asked for) ----
+  if (fit || o.reconstruction) {
     const float* fac[8];
     for (int n = 0; n < N; ++n) fac[n] = factors[n];
     // evaluated at FP32-level accuracy in every form: CUDA cores in the FP32
     // form, the three-term TF32 tensor-core product in the tensor-core forms
     // (a plain TF32 reconstruction would add ~1e-3 relative rounding per entry
-    // to the residual being measured)
-    MES_TRY(mes_reconstruct_impl(sh, core, fac, nullptr, X, sse, scr, T1, T2, d.Kmat, st,
-                                 tf32 ? MES_PREC_TF32 : MES_PREC_FP32, flags));
-    MES_TRY(mes::final_fit(normX, sse, fit, st));
+    // to the residual being measured); the same pass stores T_hat
+    MES_TRY(mes_reconstruct_impl(sh, core, fac, o.reconstruction, fit ? X : nullptr, fit ? sse : nullptr, scr, T1,
+                                 T2, d.Kmat, st, tf32 ? MES_PREC_TF32 : MES_PREC_FP32, flags));
+    if (fit) MES_TRY(mes::final_fit(normX, sse, fit, st));
   }
   return MES_OK;
 }

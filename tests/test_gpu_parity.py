@@ -576,3 +576,18 @@ def test_rate_sweep_matches_the_oracle_pipeline(mes):
         assert by[(g, 4)] < by[(g, 8)] <= by[(g, 0)] + 0.05
     for b in bits:
         assert by[(grid[0], b)] < by[(grid[1], b)]
+
+
+
+@pytest.mark.parametrize("prec,rprec", [("fp32", "fp32"), ("bf16", "tf32")])
+def test_reconstruction_from_the_fit_pass(mes, prec, rprec):
+    """T_hat stored by the fit's pass equals mes_reconstruct of the returned
+    core and factors in the same arithmetic, bit for bit."""
+    cfg, img = _scene("small_64x48")
+    T = colour.colour_convert(img, cfg["space"])
+    X = to_torch(T)
+    Xh = torch.empty_like(X)
+    res = mes.tucker_als(X, T.shape, cfg["ranks"], max_iters=4, tol=0.0, precision=prec, reconstruction=Xh)
+    ref = mes.reconstruct(res["core"], res["factors"], T.shape, cfg["ranks"], precision=rprec)
+    torch.cuda.synchronize()
+    assert torch.equal(Xh, ref)
