@@ -287,7 +287,8 @@ mes_status mes_reconstruct_impl(const Shape& sh, const float* core, const float*
     // two TF32 terms and multiplied by the three-term product, which keeps
     // FP32-level accuracy: a plain TF32 product would add ~1e-3 relative
     // error to every entry of T_hat, more than the residual being measured
-    float *U0t, *U1t, *U0h, *U0l, *U1h, *U1l, *T1h, *T1l, *T2h, *T2l;
+    float *U0t = nullptr, *U1t = nullptr, *U0h = nullptr, *U0l = nullptr, *U1h = nullptr, *U1l = nullptr;
+    float *T1h = nullptr, *T1l = nullptr, *T2h = nullptr, *T2l = nullptr;
     MES_TRY(scr.alloc(&U0t, s1 * r1));
     MES_TRY(scr.alloc(&U1t, s2 * r2));
     MES_TRY(scr.alloc(&U0h, s1 * r1));
