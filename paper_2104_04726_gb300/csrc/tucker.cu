@@ -423,13 +423,14 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (s1 * L * r2 > zsz) zsz = s1 * L * r2;
   if (r1 * r2 * Lr > zsz) zsz = r1 * r2 * Lr;
 
-  float *XB = nullptr, *P, *Ca, *Bt, *Y0 = nullptr, *Y1 = nullptr, *ctmp, *T1, *T2;
-  double *normX, *normQ, *sse, *xpart, *qpart, *fitlast;
-  int *done, *flags;
-  float* sign;
-  int* order;
+  float *XB = nullptr, *P = nullptr, *Ca = nullptr, *Bt = nullptr, *Y0 = nullptr, *Y1 = nullptr, *ctmp = nullptr;
+  float *T1 = nullptr, *T2 = nullptr;
+  double *normX = nullptr, *normQ = nullptr, *sse = nullptr, *xpart = nullptr, *qpart = nullptr, *fitlast = nullptr;
+  int *done = nullptr, *flags = nullptr;
+  float* sign = nullptr;
+  int* order = nullptr;
   const int nblk = (int)mes::grid_for(nel, 256, (int64_t)mes::sm_count() * 4);
-  float *Pt, *Cat, *Xr = nullptr, *Ur[2] = {nullptr, nullptr};
+  float *Pt = nullptr, *Cat = nullptr, *Xr = nullptr, *Ur[2] = {nullptr, nullptr};
   // BF16 form: the T-side products (P, Ca and the T-HOSVD products, whose
   // operands are T and the factors) run on BF16 copies with FP32
   // accumulation; the Y-side products (Z, W, B) run as in the TF32 form.
@@ -920,7 +921,7 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
     for (int n = 0; n < N; ++n) mes::audit_register(factors[n], (size_t)(sh.s[n] * sh.r[n]) * 4);
   }
   mes::Scratch scr(st);
-  float *T1, *T2, *Kmat;
+  float *T1 = nullptr, *T2 = nullptr, *Kmat = nullptr;
   MES_TRY(scr.alloc(&T1, sh.r1 * sh.r2 * sh.L));
   MES_TRY(scr.alloc(&T2, sh.r1 * sh.s2 * sh.L));
   MES_TRY(scr.alloc(&Kmat, 16384));
