@@ -236,8 +236,8 @@ mes_status mes_reconstruct(const float* core, const float* const* factors, int N
 
 /*
  * mes_quantize_core -- core quantiser, the rate knob of the scheme (the
- * abstract and Section I: bitrate set "by changing the rank of core tensor
- * and its quantization"; the paper does not define the quantiser).
+ * abstract and Section I set the bit rate through the core's ranks and its
+ * quantisation; the paper does not define the quantiser).
  *
  * The core (r_1 x r_2 x r_3 x ... x r_N) is cut into P = prod_{n>=3} r_n
  * planes of r_1 x r_2 (plane p is the contiguous block p of the first-mode-
@@ -252,7 +252,8 @@ mes_status mes_reconstruct(const float* core, const float* const* factors, int N
  *  bits    2..16.
  *  q       [out] int16, same element order as the core.
  *  scales  [out] FP32, P entries.
- * Errors: MES_ERR_INVALID_ARG; MES_ERR_NONFINITE if a plane holds NaN or
+ * Errors: MES_ERR_INVALID_ARG (also for more than 65535 planes or a plane of
+ *         more than 2^40 elements); MES_ERR_NONFINITE if a plane holds NaN or
  *         Inf (reported only when `status_host_sync` != 0, since it needs a
  *         device-to-host read; otherwise such planes get scale NaN).
  */
@@ -276,10 +277,13 @@ mes_status mes_quantize_core(const float* core, int N, const int64_t* ranks, int
  * allocating routine.
  *
  * Limits and behaviour:
- *  - at most 4096 planes (prod_{n>=3} r_n); more gives MES_ERR_INVALID_ARG;
+ *  - at most 4096 planes (prod_{n>=3} r_n); more gives MES_ERR_INVALID_ARG
+ *    (ranks are checked one by one, so a product that would overflow int64
+ *    is rejected too);
  *  - the first call on a device looks up the array's device address (once
- *    per device, with that device current) -- make that first call before
- *    any stream capture;
+ *    per device, with that device current) and keeps it -- make that first
+ *    call before any stream capture, and do not call this entry point on a
+ *    device after cudaDeviceReset there (the kept address is then stale);
  *  - every call shares the one array: calls whose work overlaps on the GPU
  *    (different streams without ordering) race and give wrong results; calls
  *    ordered on one stream are safe;

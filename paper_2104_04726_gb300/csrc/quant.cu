@@ -1,5 +1,6 @@
-// Core quantiser (the rate knob of the scheme: "the rank of core tensor and
-// its quantization", abstract and Section I).  Per r1 x r2 plane of the core:
+// Core quantiser (the rate knob of the scheme: the abstract and Section I set
+// the bit rate through the core's ranks and the quantisation of the core, which
+// the paper does not define further).  Per r1 x r2 plane of the core:
 // m = max|x| (exact), scale = m / qmax, q = clamp(rint(x / scale)).
 //
 // Two bandwidth passes over the core:
@@ -15,6 +16,7 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int64_t kMaxPlaneElems = (int64_t)1 << 40;   // keeps grid.x and every index in range
 
 __global__ void __launch_bounds__(kThreads)
 plane_absmax_kernel(const float* __restrict__ core, int64_t plane_size, int64_t chunk,
@@ -73,21 +75,34 @@ dequantize_kernel(const int16_t* __restrict__ q, const float* __restrict__ scale
   }
 }
 
-mes_status plane_shape(int N, const int64_t* ranks, int64_t* plane_size, int64_t* planes) {
-  if (N < 1 || N > 8 || !ranks) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: N must be 1..8");
-  for (int n = 0; n < N; ++n)
-    if (ranks[n] < 1) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: ranks must be >= 1");
-  *plane_size = ranks[0] * (N >= 2 ? ranks[1] : 1);
-  int64_t P = 1;
-  for (int n = 2; n < N; ++n) P *= ranks[n];
-  *planes = P;
-  if (P > 65535) return mes::fail(MES_ERR_INVALID_ARG, "quantiser: more than 65535 planes");
-  return MES_OK;
-}
-
 }  // namespace
 
 namespace mes {
+
+// Plane geometry: plane_size = r1 * r2 (r2 = 1 when N = 1), planes =
+// prod_{n>=3} r_n.  Each factor is checked against the limit before it is
+// multiplied in, so ranks whose product would wrap int64 are rejected rather
+// than passing the limit test as a small or negative count.
+mes_status quant_plane_shape(int N, const int64_t* ranks, int64_t max_planes, int64_t* plane_size,
+                             int64_t* planes, const char* who) {
+  if (N < 1 || N > 8 || !ranks) return fail(MES_ERR_INVALID_ARG, "%s: N must be 1..8", who);
+  for (int n = 0; n < N; ++n)
+    if (ranks[n] < 1) return fail(MES_ERR_INVALID_ARG, "%s: ranks must be >= 1", who);
+  const int64_t r1 = ranks[0], r2 = N >= 2 ? ranks[1] : 1;
+  if (r1 > kMaxPlaneElems || r2 > kMaxPlaneElems / r1)
+    return fail(MES_ERR_INVALID_ARG, "%s: a plane of %lld x %lld elements exceeds 2^40", who, (long long)r1,
+                (long long)r2);
+  int64_t P = 1;
+  for (int n = 2; n < N; ++n) {
+    if (ranks[n] > max_planes / P)
+      return fail(MES_ERR_INVALID_ARG, "%s: more than %lld planes (prod of ranks[2..])", who,
+                  (long long)max_planes);
+    P *= ranks[n];
+  }
+  *plane_size = r1 * r2;
+  *planes = P;
+  return MES_OK;
+}
 
 // Launches both passes; maxbits must hold `planes` words and is cleared here.
 mes_status quantize_launch(const float* core, int64_t plane_size, int64_t planes, int bits,
@@ -118,7 +133,7 @@ extern "C" mes_status mes_quantize_core(const float* core, int N, const int64_t*
   if (!core || !q || !scales) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core: null pointer");
   if (bits < 2 || bits > 16) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core: bits must be 2..16");
   int64_t plane_size = 0, planes = 0;
-  MES_TRY(plane_shape(N, ranks, &plane_size, &planes));
+  MES_TRY(mes::quant_plane_shape(N, ranks, 65535, &plane_size, &planes, "mes_quantize_core"));   // grid.y limit
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::Scratch scratch(st);
   unsigned* maxbits = nullptr;
@@ -146,7 +161,7 @@ extern "C" mes_status mes_dequantize_core(const int16_t* q, const float* scales,
   mes::clear_error();
   if (!core || !q || !scales) return mes::fail(MES_ERR_INVALID_ARG, "mes_dequantize_core: null pointer");
   int64_t plane_size = 0, planes = 0;
-  MES_TRY(plane_shape(N, ranks, &plane_size, &planes));
+  MES_TRY(mes::quant_plane_shape(N, ranks, 65535, &plane_size, &planes, "mes_dequantize_core"));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t total = plane_size * planes;
   mes::ProfScope prof("dequantize", st, 0.0, 6.0 * total);

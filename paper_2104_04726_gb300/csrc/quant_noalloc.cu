@@ -12,7 +12,10 @@
 //
 // The host never dereferences the array: its name in host code is only a
 // handle, so the device address is looked up with cudaGetSymbolAddress, once
-// per device, with that device current, and cached.
+// per device, with that device current, and cached.  The cache assumes the
+// library's module stays loaded: after cudaDeviceReset on a device the cached
+// address is stale, so a process that resets a device must not call this
+// entry point on it again.
 #include <mutex>
 
 #include "small.cuh"
@@ -62,16 +65,10 @@ extern "C" mes_status mes_quantize_core_noalloc(const float* core, int N, const 
     return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core_noalloc: null pointer");
   if (bits < 2 || bits > 16)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core_noalloc: bits must be 2..16");
-  if (N < 1 || N > 8) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core_noalloc: N must be 1..8");
-  for (int n = 0; n < N; ++n)
-    if (ranks[n] < 1) return mes::fail(MES_ERR_INVALID_ARG, "mes_quantize_core_noalloc: ranks must be >= 1");
-  const int64_t plane_size = ranks[0] * (N >= 2 ? ranks[1] : 1);
-  int64_t planes = 1;
-  for (int n = 2; n < N; ++n) planes *= ranks[n];
-  if (planes > kMaxPlanes)
-    return mes::fail(MES_ERR_INVALID_ARG,
-                     "mes_quantize_core_noalloc: %lld planes exceed the fixed scratch of %lld planes; "
-                     "use mes_quantize_core", (long long)planes, (long long)kMaxPlanes);
+  int64_t plane_size = 0, planes = 0;
+  // rejects more than kMaxPlanes planes, checking each rank before it is
+  // multiplied in (a wrapped product must not pass the limit)
+  MES_TRY(mes::quant_plane_shape(N, ranks, kMaxPlanes, &plane_size, &planes, "mes_quantize_core_noalloc"));
   unsigned* maxbits = nullptr;
   MES_TRY(scratch_address(&maxbits));
   // quantize_launch clears the `planes` words it uses before the two passes

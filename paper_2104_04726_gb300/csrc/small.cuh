@@ -83,6 +83,10 @@ mes_status eig_mid(const float* H, int r, float* Z, const int* skip, cudaStream_
 mes_status colour_launch(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K, int space,
                          float gamma, float* out, double* partials, double* norm2, cudaStream_t st);
 unsigned colour_grid(int64_t npix, int64_t K);
+// Validated plane geometry of the quantiser (plane_size = r1 r2, planes =
+// prod_{n>=3} r_n <= max_planes), without int64 overflow.
+mes_status quant_plane_shape(int N, const int64_t* ranks, int64_t max_planes, int64_t* plane_size,
+                             int64_t* planes, const char* who);
 mes_status quantize_launch(const float* core, int64_t plane_size, int64_t planes, int bits,
                            int16_t* q, float* scales, unsigned* maxbits, cudaStream_t st);
 

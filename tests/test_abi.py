@@ -171,3 +171,18 @@ def test_rate_bits_counts_core_scales_and_factors():
     assert mes.rate_bits(dims, ranks, 8) == 16 * 12 * 18 * 8 + 18 * 32 + factors * 16
     assert mes.rate_bits(dims, ranks, 0) == 16 * 12 * 18 * 32 + factors * 16
     assert mes.rate_bits(dims, ranks, 4, factor_bits=8) == 16 * 12 * 18 * 4 + 18 * 32 + factors * 8
+
+
+def test_quantiser_plane_count_cannot_wrap(lib):
+    """Ranks whose product would overflow int64 are rejected before anything
+    is enqueued (e.g. (1, 1, 2^62, 2) wraps to a negative plane count), by
+    both quantiser entry points and the dequantiser; so are plane counts just
+    above each entry point's limit (4096 without allocation, 65535 with)."""
+    fake = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    for ranks in ([1, 1, 1 << 62, 2], [1, 1, 2, 1 << 62], [3, 5, 1 << 40, 1 << 40], [1 << 40, 1 << 30],
+                  [2, 2, 65536]):
+        assert lib.mes_quantize_core(fake, len(ranks), _i64(ranks), 8, fake, fake, 0, None) == 1, ranks
+        assert lib.mes_dequantize_core(fake, fake, len(ranks), _i64(ranks), fake, None) == 1, ranks
+        assert lib.mes_quantize_core_noalloc(fake, len(ranks), _i64(ranks), 8, fake, fake, None) == 1, ranks
+    assert lib.mes_quantize_core_noalloc(fake, 3, _i64([2, 2, 4097]), 8, fake, fake, None) == 1
+    assert b"4096 planes" in lib.mes_last_error()

@@ -64,3 +64,18 @@ def test_rejects_more_planes_than_its_fixed_scratch(lib):
     with pytest.raises(lib.MesError) as e:
         _quant(lib, "noalloc", core, (2, 2, 4097), 8)
     assert e.value.name == "MES_ERR_INVALID_ARG"
+
+
+@pytest.mark.parametrize("ranks", [(8, 8, 4096), (37, 29)])
+def test_largest_plane_count_and_order_two_core(lib, ranks):
+    """Exactly 4096 planes, where the fixed scratch is used to its last word,
+    and an order-2 core (one plane, no trailing modes): the same codes and
+    scales as the allocating quantiser, on two calls in a row."""
+    rng = np.random.default_rng(sum(ranks))
+    for call in range(2):
+        core_np = (rng.standard_normal(ranks[::-1]) * (10.0 ** (2 - 2 * call))).astype(np.float32)
+        core = torch.from_numpy(core_np).cuda()
+        q_ref, s_ref = _quant(lib, "alloc", core, ranks, 10)
+        q, s = _quant(lib, "noalloc", core, ranks, 10)
+        assert np.array_equal(s, s_ref), (ranks, call)
+        assert np.array_equal(q, q_ref), (ranks, call)
