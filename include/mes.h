@@ -146,8 +146,12 @@ typedef struct mes_als_opts {
   int precision;        /* mes_precision of the large contractions (FP32).
                            The Gram and orthonormalisation products of the
                            factor update stay FP32 in every form.           */
-  int init_iters;       /* subspace steps of the T-HOSVD initialisation (2)   */
-  int inner_iters;      /* subspace steps per factor update in a sweep (1)    */
+  int init_iters;       /* subspace steps of the T-HOSVD initialisation
+                           (default 2; 24 when max_iters <= 2)                */
+  int inner_iters;      /* subspace steps per factor update in a sweep
+                           (default 1; 12 when max_iters <= 2: a run of one
+                           or two sweeps needs each update close to the exact
+                           eigenvectors, later sweeps refine them anyway)     */
   uint64_t seed;        /* seed of the random start block of the init (1)     */
   const float* const* init_factors; /* nullable: device factors to start from
                                        instead of T-HOSVD (warm start / resume) */
@@ -164,6 +168,18 @@ typedef struct mes_als_opts {
                            returned decomposition, from the same pass that
                            measures the fit (as mes_reconstruct gives with
                            precision FP32 for the FP32 form, TF32 otherwise) */
+  int* status;          /* nullable device int, written at the end of the call
+                           (stream-ordered): MES_OK, or a failure found on the
+                           device -- MES_ERR_TIMEOUT when a bounded tensor-core
+                           pipeline wait gave up, MES_ERR_NONFINITE when
+                           ||T||^2 or the fit is not finite (NaN or Inf in T).
+                           On either failure *fit is NaN, status or not.  The
+                           host call itself cannot see these (it returns
+                           before the device runs).                           */
+  int64_t wait_ns;      /* bound of every tensor-core pipeline wait, in ns (0:
+                           2 s).  A wait that runs out sets the timeout status
+                           and the kernel finishes without hanging; a bound of
+                           a few ns forces that path (tests of error handling) */
 } mes_als_opts;
 
 /*
@@ -185,11 +201,14 @@ typedef struct mes_als_opts {
  *  factors  [in]  HOST array of N DEVICE pointers; factors[n] [out] receives
  *                 S^(n), column-major s_n x r_n.
  *  fit      [out] nullable device double: 1 - ||T - T_hat||_F / ||T||_F of the
- *                 returned decomposition, from the explicit residual.
+ *                 returned decomposition, from the explicit residual; NaN
+ *                 when the device met a failure (see opts->status).
  *  opts           nullable, see mes_als_opts.
- * Errors: MES_ERR_INVALID_ARG (null pointers, N out of range, bad sizes or
- *         options), MES_ERR_RANK (rank constraints), MES_ERR_OOM,
- *         MES_ERR_CUDA.
+ * Errors (returned): MES_ERR_INVALID_ARG (null pointers, N out of range, bad
+ *         sizes or options), MES_ERR_RANK (rank constraints), MES_ERR_OOM,
+ *         MES_ERR_CUDA.  Failures the device meets while the enqueued work
+ *         runs (a pipeline wait that ran out, NaN or Inf in T) arrive in
+ *         opts->status and as a NaN fit.
  */
 mes_status mes_tucker_als(const float* X, int N, const int64_t* dims, const int64_t* ranks,
                           int max_iters, double tol, float* core, float* const* factors,
@@ -219,7 +238,8 @@ mes_status mes_tucker_als_workspace_size(int N, const int64_t* dims, const int64
  *  out      [out] FP32 tensor of dims `dims`.
  *  ref      [in]  nullable FP32 tensor of dims `dims`; when given, sse
  *                 receives sum((ref - out)^2) in FP64 (fused into the last
- *                 contraction; bitwise reproducible).
+ *                 contraction; bitwise reproducible), or NaN if a tensor-core
+ *                 pipeline wait gave up.
  *  sse      [out] nullable device double.
  *  precision      MES_PREC_FP32: every product on CUDA cores in FP32;
  *                 MES_PREC_TF32 or MES_PREC_BF16: the two large products on
@@ -343,6 +363,9 @@ typedef struct mes_problem {
  *   happens outside the capture.  The graph holds the problems' pointers.
  * mes_batch_launch(b, stream): replays the captured graph on `stream`.
  * mes_batch_destroy(b): frees the context (after its work completes).
+ * Failures the device meets while a problem runs (a tensor-core wait that ran
+ * out, NaN or Inf in its tensor) arrive in that problem's opts.status (when
+ * set) and as a NaN fit; `statuses` only reports validation and enqueue.
  * Errors: MES_ERR_INVALID_ARG (null handle or arrays, n < 1, a problem that
  *   fails validation, launch without capture, capture while the kernel
  *   profiler is on), errors of the single calls, MES_ERR_CUDA.
@@ -372,7 +395,10 @@ mes_status mes_batch_destroy(mes_batch* b);
  *   *ticket receives its id.  MES_ERR_OOM if it can never fit the budget.
  * mes_serve_poll(s, ticket, done, result, latency_ms): HOST outputs; *done 1
  *   once the request's device work has completed, with its status and its
- *   latency from submission to observed completion (nullable outputs).
+ *   latency from submission to observed completion (nullable outputs).  The
+ *   status includes failures met on the device (MES_ERR_TIMEOUT,
+ *   MES_ERR_NONFINITE; the server reads the request's opts.status word, or a
+ *   word of its own when the request gives none, after completion).
  * mes_serve_wait(s, ticket, timeout_ms, result, latency_ms): blocks until
  *   done or timeout_ms (< 0: no limit); MES_ERR_TIMEOUT on timeout.
  * mes_serve_get_stats(s, out): counts, latency percentiles of completed

@@ -117,7 +117,7 @@ def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=N
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
                precision: str = "fp32", init_iters: int = 0, inner_iters: int = 0, seed: int = 0,
                canonical: bool = True, init_factors=None, history: bool = False, outputs=None,
-               init: str = "thosvd", reconstruction=None):
+               init: str = "thosvd", reconstruction=None, wait_ns: int = 0):
     """Tucker-ALS / HOOI (Section III-B).  X: float32 CUDA tensor holding the
     first-mode-fastest tensor of paper dims `dims`.  Returns a dict with
     `core` (torch shape reversed(ranks)), `factors` (list of (r_n, s_n)
@@ -125,7 +125,10 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     (int32 CUDA scalar) and, if history, `fit_history` (max_iters float64).
     init: "thosvd" (truncated HOSVD) or "interlaced" (interlaced HOSVD); a
     given `init_factors` overrides both.  reconstruction: optional float32
-    CUDA tensor like X that receives T_hat (Eq. 1) from the fit's pass."""
+    CUDA tensor like X that receives T_hat (Eq. 1) from the fit's pass.
+    `status` (int32 CUDA scalar) receives the device-side status (0, or
+    MES_ERR_TIMEOUT / MES_ERR_NONFINITE, with a NaN fit); wait_ns bounds the
+    tensor-core pipeline waits (0: the library default)."""
     torch = _torch()
     _need(X, torch.float32, "X")
     dims = [int(d) for d in dims]
@@ -147,6 +150,7 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
         hist = torch.full((max_iters,), float("nan"), dtype=torch.float64, device=dev) if history else None
     else:
         core, factors, fit, iters, hist = outputs
+    status = torch.zeros((), dtype=torch.int32, device=dev)
     fac_arr = (ctypes.c_void_p * N)(*[f.data_ptr() for f in factors])
     opts = _lib.MesAlsOpts()
     opts.precision = PRECISIONS[precision]
@@ -162,6 +166,8 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
         opts.reconstruction = reconstruction.data_ptr()
     opts.iters_done = iters.data_ptr()
     opts.fit_history = hist.data_ptr() if hist is not None else None
+    opts.status = status.data_ptr()
+    opts.wait_ns = int(wait_ns)
     keep = None
     if init_factors is not None:
         keep = (ctypes.c_void_p * N)(*[f.data_ptr() for f in init_factors])
@@ -170,7 +176,7 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     st = lib.mes_tucker_als(_ptr(X), N, _i64(dims), _i64(ranks), int(max_iters), float(tol), _ptr(core),
                             fac_arr, _ptr(fit), ctypes.byref(opts), _stream())
     _lib.check(st, "mes_tucker_als")
-    out = {"core": core, "factors": factors, "fit": fit, "iters": iters}
+    out = {"core": core, "factors": factors, "fit": fit, "iters": iters, "status": status}
     if hist is not None:
         out["fit_history"] = hist
     return out
@@ -294,7 +300,7 @@ class Problem:
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], X=None, rgb8=None, space: str = "ipt",
                  gamma: float = 2.2, max_iters: int = 20, tol: float = 0.0, precision: str = "fp32",
-                 quant_bits: int = 0, device=None):
+                 quant_bits: int = 0, device=None, wait_ns: int = 0):
         torch = _torch()
         dims = [int(d) for d in dims]
         ranks = [int(r) for r in ranks]
@@ -316,6 +322,7 @@ class Problem:
         self.factors = [torch.empty((r, s), dtype=torch.float32, device=dev) for s, r in zip(dims, ranks)]
         self.fit = torch.empty((), dtype=torch.float64, device=dev)
         self.iters = torch.zeros((), dtype=torch.int32, device=dev)
+        self.status = torch.zeros((), dtype=torch.int32, device=dev)   # device-side status of the decomposition
         P = 1
         for r in ranks[2:]:
             P *= r
@@ -335,6 +342,8 @@ class Problem:
         p.tol = float(tol)
         p.opts.precision = PRECISIONS[precision]
         p.opts.iters_done = self.iters.data_ptr()
+        p.opts.status = self.status.data_ptr()
+        p.opts.wait_ns = int(wait_ns)
         p.core = _ptr(self.core)
         p.fit = _ptr(self.fit)
         p.quant_bits = int(quant_bits)

@@ -73,6 +73,8 @@ class MesAlsOpts(ctypes.Structure):
         ("canonical", ctypes.c_int),
         ("init", ctypes.c_int),
         ("reconstruction", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+        ("wait_ns", ctypes.c_int64),
     ]
 
 

@@ -263,6 +263,11 @@ struct mes_server {
   std::vector<cudaStream_t> slots;
   std::vector<cudaEvent_t> slot_done;
   std::vector<uint64_t> slot_req;   // 0 = free
+  // per slot: the device-side status word of the running decomposition
+  // (used when the request brings none) and its pinned host copy, read once
+  // the slot's completion event has fired
+  int* dev_status = nullptr;
+  int* host_status = nullptr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;
@@ -299,6 +304,8 @@ void serve_loop(mes_server* s) {
       if (q != cudaSuccess) {
         cudaGetLastError();
         r.status = MES_ERR_CUDA;
+      } else if (s->host_status[k] != MES_OK) {
+        r.status = static_cast<mes_status>(s->host_status[k]);   // failure met on the device
       }
       const auto now = Clock::now();
       r.latency_ms = 1e3 * secs(r.submitted, now);
@@ -333,15 +340,30 @@ void serve_loop(mes_server* s) {
       const uint64_t id = *it;
       s->queue.erase(it);
       Request& r = s->reqs[id];   // node-based map: the reference stays valid
+      if (mes::fault_admit()) {
+        // injected refusal: the request ends without running
+        r.done = true;
+        r.status = MES_ERR_OOM;
+        r.latency_ms = 1e3 * secs(r.submitted, Clock::now());
+        ++s->failed;
+        s->cv_done.notify_all();
+        progressed = true;
+        continue;
+      }
       s->slot_req[k] = id;
       s->in_use += r.bytes;
       s->peak = std::max(s->peak, s->in_use);
       r.slot = k;
-      const mes_problem prob = r.p;
+      mes_problem prob = r.p;
+      int* dstat = prob.opts.status ? prob.opts.status : s->dev_status + k;
+      prob.opts.status = dstat;
+      s->host_status[k] = MES_OK;
       if (s->first_admit < 0) s->first_admit = secs(s->t0, Clock::now());
       lk.unlock();
       mes_status st = problem_enqueue(prob, s->slots[k]);
-      if (st == MES_OK && cudaEventRecord(s->slot_done[k], s->slots[k]) != cudaSuccess) {
+      if (st == MES_OK && (cudaMemcpyAsync(s->host_status + k, dstat, sizeof(int), cudaMemcpyDeviceToHost,
+                                           s->slots[k]) != cudaSuccess ||
+                           cudaEventRecord(s->slot_done[k], s->slots[k]) != cudaSuccess)) {
         cudaGetLastError();
         st = MES_ERR_CUDA;
       }
@@ -400,6 +422,17 @@ extern "C" mes_status mes_serve_create(size_t hbm_budget_bytes, int max_slots, m
     }
     s->slot_req.push_back(0);
   }
+  // status words, allocated once here (never while serving)
+  if (cudaMalloc(&s->dev_status, sizeof(int) * max_slots) != cudaSuccess ||
+      cudaMallocHost(&s->host_status, sizeof(int) * max_slots) != cudaSuccess) {
+    cudaGetLastError();
+    if (s->dev_status) cudaFree(s->dev_status);
+    for (cudaStream_t x : s->slots) cudaStreamDestroy(x);
+    for (cudaEvent_t x : s->slot_done) cudaEventDestroy(x);
+    delete s;
+    return mes::fail(MES_ERR_OOM, "mes_serve_create: status words could not be allocated");
+  }
+  for (int k = 0; k < max_slots; ++k) s->host_status[k] = MES_OK;
   s->worker = std::thread(serve_loop, s);
   *out = s;
   return MES_OK;
@@ -514,6 +547,8 @@ extern "C" mes_status mes_serve_destroy(mes_server* s) {
   cudaSetDevice(s->device);
   for (cudaStream_t x : s->slots) cudaStreamDestroy(x);
   for (cudaEvent_t x : s->slot_done) cudaEventDestroy(x);
+  if (s->dev_status) cudaFree(s->dev_status);
+  if (s->host_status) cudaFreeHost(s->host_status);
   cudaSetDevice(prev);
   cudaGetLastError();
   delete s;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -48,9 +49,23 @@ __host__ __device__ __forceinline__ uint16_t bf16_bits(float x) {
   return (uint16_t)(u >> 16);
 }
 
+// Key of the rank-by-count sorts (eigenvalues, Gram diagonals): NaN maps
+// below every number, so "greater, or equal with a lower index" stays a
+// strict total order and the ranks form a permutation even when a failed
+// step upstream has left NaN in the data.
+__host__ __device__ __forceinline__ float order_key(float w) { return w == w ? w : -INFINITY; }
+__host__ __device__ __forceinline__ double order_key(double w) { return w == w ? w : -(double)INFINITY; }
+
 // Records a formatted message in the thread-local error buffer and returns s.
 mes_status fail(mes_status s, const char* fmt, ...);
 void clear_error();
+
+// Host-side fault injection (environment variable MES_FAULT, read at each
+// use): fault_alloc(k) is true when allocation k of the current ABI call must
+// fail ("alloc:<k>"); fault_admit() when the serving loop must refuse
+// admissions ("admit").
+bool fault_alloc(int index);
+bool fault_admit();
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
@@ -117,6 +132,7 @@ struct Scratch {
       return MES_OK;
     }
     if (n >= 64) return fail(MES_ERR_OOM, "scratch table full");
+    if (fault_alloc(n)) return fail(MES_ERR_OOM, "allocation %d refused (fault injected by MES_FAULT)", n);
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, rounded, stream);
     if (e != cudaSuccess) {

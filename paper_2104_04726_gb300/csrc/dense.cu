@@ -949,10 +949,10 @@ __global__ void eig_small_kernel(const double* __restrict__ Gin, int n, int r, f
   }
   // order by descending eigenvalue (stable in index), real entries only
   if (lane < n) {
-    const double w = A[lane][lane];
+    const double w = mes::order_key(A[lane][lane]);
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double wj = A[j][j];
+      const double wj = mes::order_key(A[j][j]);
       if (wj > w || (wj == w && j < lane)) ++rank;
     }
     order[rank] = lane;
@@ -1065,10 +1065,10 @@ eig_mid_kernel(const float* __restrict__ Hin, int r, float* __restrict__ Z, cons
   }
   // sort by descending diagonal (only the r real entries)
   for (int i = t; i < r; i += kMid) {
-    float w = A[i * ld + i];
+    const float w = mes::order_key(A[i * ld + i]);
     int rank = 0;
     for (int j = 0; j < r; ++j) {
-      float wj = A[j * ld + j];
+      const float wj = mes::order_key(A[j * ld + j]);
       if (wj > w || (wj == w && j < i)) ++rank;
     }
     for (int row = 0; row < r; ++row) Z[row + r * rank] = V[row * ld + i];

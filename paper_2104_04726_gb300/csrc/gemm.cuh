@@ -47,6 +47,8 @@ struct Gemm {
   // summed in a fixed order).  Used when the tile grid leaves most SMs idle.
   float* split_ws = nullptr;
   int64_t split_elems = 0;
+  // Bound of each pipeline wait of the tensor-core kernel in ns (0: 2 s).
+  uint64_t wait_ns = 0;
 };
 
 // FP32 CUDA-core path.

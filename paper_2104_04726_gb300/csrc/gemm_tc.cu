@@ -19,7 +19,11 @@
 // product), so the result has FP32-level accuracy.  Split-K over
 // grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
 // result is deterministic.  Every mbarrier wait is bounded (globaltimer,
-// 2 s); a timeout sets an error bit and the CTA tears down normally.
+// 2 s unless the caller sets a shorter bound); a timeout sets an error bit.
+// Before the CTA frees its tensor memory and exits, the producer waits for
+// every TMA load it issued and the MMA thread for its committed MMAs, both
+// again bounded (kDrainNs), so no copy or MMA is left writing into shared or
+// tensor memory the CTA no longer owns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -40,7 +44,8 @@ namespace {
 constexpr int BM = 128;
 constexpr int kThreads = 320;   // 2 control warps + 8 epilogue warps
 constexpr int kEpiWarps = 8;
-constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kWaitNs = 2000000000ull;    // default bound of a pipeline wait
+constexpr uint64_t kDrainNs = 2000000000ull;   // bound of the teardown waits for work in flight
 
 struct TcArgs {
   int64_t M, N;
@@ -58,6 +63,7 @@ struct TcArgs {
   float* split_ws;     // [split][batch][M][N] when splits > 1
   const int* skip;
   int* err;
+  uint64_t wait_ns;    // bound of each pipeline wait (0: kWaitNs)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -93,12 +99,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false after kWaitNs without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: false after limit_ns without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -254,16 +260,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
+  const uint64_t wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
     int stage = 0;
     uint32_t phase = 0;
+    uint32_t issued = 0, last_phase = 0;   // per stage: loaded at least once; parity of its last load
     for (int i = 0; i < nkt; ++i) {
-      if (!mbar_wait(&empty[stage], phase ^ 1u)) {
+      if (!mbar_wait(&empty[stage], phase ^ 1u, wait_ns)) {
         ok = false;
         break;
       }
+      issued |= 1u << stage;
+      last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
       const int kt = kt_begin + i;
       const int kh = kt / args.k_tiles_lo;
       const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
@@ -282,12 +292,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
     }
     if (!ok) atomicOr(args.err, 8);
+    // teardown: every load this thread issued has landed (a stage whose last
+    // phase already completed returns at once)
+    for (int s2 = 0; s2 < STAGES; ++s2)
+      if (((issued >> s2) & 1u) && !mbar_wait(&full[s2], (last_phase >> s2) & 1u, kDrainNs))
+        atomicOr(args.err, 64);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     int stage = 0;
     uint32_t phase = 0;
     for (int i = 0; i < nkt; ++i) {
-      if (!mbar_wait(&full[stage], phase)) {
+      if (!mbar_wait(&full[stage], phase, wait_ns)) {
         ok = false;
         break;
       }
@@ -314,13 +329,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
     mma_commit(accum);
     if (!ok) atomicOr(args.err, 16);
+    // teardown: the MMAs issued above are complete before TMEM is freed
+    if (!mbar_wait(accum, 0, kDrainNs)) atomicOr(args.err, 64);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const int wq = warp & 3;                 // TMEM lane quarter = rows wq*32 .. wq*32+31
     const int half = (warp - 2) >> 2;        // columns half*BN/2 .. (half+1)*BN/2 - 1
     const int64_t m = m0 + wq * 32 + lane;
     // warp-uniform: the transposed stores below shuffle across the warp
-    const bool waited = __all_sync(0xffffffffu, mbar_wait(accum, 0));
+    const bool waited = __all_sync(0xffffffffu, mbar_wait(accum, 0, wait_ns));
     if (!waited && lane == 0) atomicOr(args.err, 32);
     tc_fence_after();
     const bool mok = m < args.M;
@@ -599,6 +616,7 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   a.partials = g.partials;
   a.skip = g.skip;
   a.err = err;
+  a.wait_ns = g.wait_ns;
   // split K when the tile grid leaves most SMs idle
   const int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + bn - 1) / bn) * g.batch;
   int splits = 1;

@@ -268,7 +268,8 @@ __global__ void fit_flag_kernel(const double* __restrict__ normX, const double* 
                                 int* __restrict__ done, int* __restrict__ iters) {
   if (*done) return;
   double nx = *normX, nq = *normQ;
-  double fit = (nx > 0.0) ? 1.0 - sqrt(fmax(nx - nq, 0.0)) / sqrt(nx) : 1.0;
+  // T = 0 fits exactly; a non-finite ||T||^2 (NaN or Inf in T) gives NaN
+  double fit = (nx > 0.0 && isfinite(nx)) ? 1.0 - sqrt(fmax(nx - nq, 0.0)) / sqrt(nx) : (nx == 0.0 ? 1.0 : NAN);
   if (hist) hist[sweep - 1] = fit;
   if (iters) *iters = sweep;
   if (sweep > 1 && fabs(fit - *last) < tol) *done = 1;
@@ -277,8 +278,22 @@ __global__ void fit_flag_kernel(const double* __restrict__ normX, const double* 
 
 __global__ void final_fit_kernel(const double* __restrict__ normX, const double* __restrict__ sse,
                                  double* __restrict__ fit) {
-  double nx = *normX;
-  *fit = (nx > 0.0) ? 1.0 - sqrt(fmax(*sse, 0.0)) / sqrt(nx) : 1.0;
+  double nx = *normX, e = *sse;
+  *fit = (nx > 0.0 && isfinite(nx)) ? 1.0 - sqrt(fmax(e, 0.0)) / sqrt(nx) : (nx == 0.0 ? 1.0 : NAN);
+  if (!(e == e)) *fit = NAN;   // fmax would hide a NaN residual
+}
+
+// Status of a decomposition from what the device recorded: a bounded
+// tensor-core pipeline wait that gave up (error bits 8..64) is a timeout;
+// a non-finite ||T||^2 or fit is NAN/Inf in the data.  On failure the fit is
+// set to NaN so no caller mistakes the result for a valid one.
+__global__ void finish_status_kernel(const int* __restrict__ flags, const double* __restrict__ normX,
+                                     double* __restrict__ fit, int* __restrict__ status) {
+  int code = MES_OK;
+  if (flags[0] & (8 | 16 | 32 | 64)) code = MES_ERR_TIMEOUT;
+  else if (normX && (!isfinite(*normX) || (fit && !isfinite(*fit)))) code = MES_ERR_NONFINITE;
+  if (code != MES_OK && fit) *fit = NAN;
+  if (status) *status = code;
 }
 
 // Per column q of U (s x r): the sign that makes its largest-magnitude entry
@@ -316,10 +331,10 @@ col_sign_kernel(const float* __restrict__ U, int64_t s, float* __restrict__ sign
 __global__ void diag_order_kernel(const float* __restrict__ H, int r, int* __restrict__ src_of) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= r) return;
-  float w = H[i + (int64_t)r * i];
+  const float w = mes::order_key(H[i + (int64_t)r * i]);
   int rank = 0;
   for (int j = 0; j < r; ++j) {
-    float wj = H[j + (int64_t)r * j];
+    const float wj = mes::order_key(H[j + (int64_t)r * j]);
     if (wj > w || (wj == w && j < i)) ++rank;
   }
   src_of[rank] = i;
@@ -333,6 +348,7 @@ __global__ void permute_cols_kernel(const float* __restrict__ Uin, int64_t s, in
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t q = e / s, i = e - q * s;
     int src = src_of ? src_of[q] : (int)q;
+    src = min(max(src, 0), r - 1);   // a gather index never leaves the matrix
     float sg = sign ? sign[q] : 1.f;
     Uout[e] = sg * Uin[i + s * src];
   }
@@ -346,6 +362,7 @@ __global__ void permute_core_kernel(const float* __restrict__ in, int64_t total,
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t q = (e / stride) % r;
     int src = src_of ? src_of[q] : (int)q;
+    src = min(max(src, 0), r - 1);   // a gather index never leaves the tensor
     float sg = sign ? sign[q] : 1.f;
     out[e] = sg * in[e + (src - q) * stride];
   }
@@ -501,6 +518,19 @@ mes_status fit_flag(const double* normX, const double* normQ, int sweep, double 
 mes_status final_fit(const double* normX, const double* sse, double* fit, cudaStream_t st) {
   ProfScope prof("fit_flag", st, 0.0, 0.0);
   final_fit_kernel<<<1, 1, 0, st>>>(normX, sse, fit);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status nan_on_timeout(const int* flags, double* x, cudaStream_t st) {
+  finish_status_kernel<<<1, 1, 0, st>>>(flags, nullptr, x, nullptr);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status finish_status(const int* flags, const double* normX, double* fit, int* status, cudaStream_t st) {
+  ProfScope prof("fit_flag", st, 0.0, 0.0);
+  finish_status_kernel<<<1, 1, 0, st>>>(flags, normX, fit, status);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

@@ -58,6 +58,12 @@ mes_status small_gram(const Fibres& fb, const float* Kmat, int L, int L2, int sn
 mes_status fit_flag(const double* normX, const double* normQ, int sweep, double tol, double* hist,
                     double* last, int* done, int* iters, cudaStream_t st);
 mes_status final_fit(const double* normX, const double* sse, double* fit, cudaStream_t st);
+// status (nullable device int) = MES_OK, MES_ERR_TIMEOUT (pipeline wait
+// bits in flags[0]) or MES_ERR_NONFINITE (||T||^2 or fit not finite); the
+// fit (nullable) becomes NaN on failure
+mes_status finish_status(const int* flags, const double* normX, double* fit, int* status, cudaStream_t st);
+// *x = NaN when flags[0] holds a pipeline-wait bit (x: an FP64 result such as a residual)
+mes_status nan_on_timeout(const int* flags, double* x, cudaStream_t st);
 mes_status col_signs(const float* U, int64_t s, int r, float* sign, cudaStream_t st);
 mes_status diag_order(const float* H, int r, int* src_of, cudaStream_t st);
 mes_status permute_cols(const float* Uin, int64_t s, int r, const int* src_of, const float* sign,

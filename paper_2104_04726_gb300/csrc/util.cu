@@ -1,5 +1,6 @@
 // Error buffer, device queries and the version string.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -19,6 +20,32 @@ mes_status fail(mes_status s, const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+// Host-side fault injection for tests of the failure paths: MES_FAULT is a
+// comma-separated list of "alloc:<k>" (allocation number k of each ABI call
+// fails as if the device were out of memory) and "admit" (the serving loop
+// refuses every admission).  Nothing here touches the GPU.
+static bool fault_item(const char* name, long* arg) {
+  const char* e = getenv("MES_FAULT");
+  if (!e || !*e) return false;
+  const size_t n = strlen(name);
+  for (const char* p = e; p && *p;) {
+    if (strncmp(p, name, n) == 0 && (p[n] == 0 || p[n] == ',' || p[n] == ':')) {
+      if (arg) *arg = (p[n] == ':') ? strtol(p + n + 1, nullptr, 10) : 0;
+      return true;
+    }
+    p = strchr(p, ',');
+    if (p) ++p;
+  }
+  return false;
+}
+
+bool fault_alloc(int index) {
+  long k = 0;
+  return fault_item("alloc", &k) && k == index;
+}
+
+bool fault_admit() { return fault_item("admit", nullptr); }
 
 int sm_count() {
   static int cached[64] = {0};

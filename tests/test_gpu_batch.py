@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import synth
+from oracle import colour, tucker
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +81,36 @@ def _same(p, ref, bits):
 
 
 @pytest.fixture(scope="module")
+def oracle_fits(cases):
+    """The FP64 oracle's fit of every stack of the batch (its own colour
+    pre-pass of the 8-bit images, or the FP32 tensor read back), exact HOOI
+    with the problems' sweep count."""
+    specs, probs, _ = cases
+    fits = []
+    for p, spec in zip(probs, specs):
+        dims, ranks, kind, space, prec, bits, seed = spec
+        if p.rgb8 is not None:
+            T = colour.colour_convert(p.rgb8.cpu().numpy(), space)
+        else:
+            a = p.X.cpu().numpy().astype(np.float64)
+            T = a.transpose(tuple(range(a.ndim))[::-1])
+        fits.append(tucker.hooi(T, ranks, 8, 0.0).fit)
+    return fits
+
+
+def _against_oracle(probs, specs, fits, where):
+    """Each stack's fit against the oracle's after the same 8 sweeps: 1e-4
+    relative (the GPU's default of one warm-started subspace step per update
+    trails exact HOOI's first sweeps by up to ~5e-5 on these scenes and
+    reaches the same fixed point; the tensor-core target is 1e-4 as well)."""
+    torch.cuda.synchronize()
+    for p, spec, fo in zip(probs, specs, fits):
+        f = float(p.fit)
+        print(f"{where} {spec[0]} {spec[4]}: fit {f:.9f} oracle {fo:.9f} rel {abs(f - fo) / fo:.2e}")
+        assert abs(f - fo) / fo < 1e-4, (spec, f, fo)
+
+
+@pytest.fixture(scope="module")
 def cases(mes):
     specs = _specs()
     probs = [_problem(mes, s) for s in specs]
@@ -106,6 +137,16 @@ def test_batch_matches_single_calls(mes, cases):
     b.close()
 
 
+def test_batch_stacks_against_the_oracle(mes, cases, oracle_fits):
+    specs, probs, refs = cases
+    for p in probs:
+        _clear(p)
+    b = mes.Batch(3)
+    b.run(probs)
+    _against_oracle(probs, specs, oracle_fits, "batch")
+    b.close()
+
+
 def test_batch_graph_replay(mes, cases):
     specs, probs, refs = cases
     b = mes.Batch(4)
@@ -125,7 +166,7 @@ def test_batch_graph_replay(mes, cases):
     b.close()
 
 
-def test_server_results_alone_and_in_mix(mes, cases):
+def test_server_results_alone_and_in_mix(mes, cases, oracle_fits):
     specs, probs, refs = cases
     for p in probs:
         _clear(p)
@@ -137,6 +178,7 @@ def test_server_results_alone_and_in_mix(mes, cases):
         assert status == 0 and lat > 0
     for p, r, s in zip(probs, refs, specs):
         _same(p, r, s[5])
+    _against_oracle(probs, specs, oracle_fits, "served")
     st = srv.stats()
     assert st["completed"] == len(probs) and st["failed"] == 0 and st["queued"] == 0
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]

@@ -64,6 +64,26 @@ def gap_and_sin(T, ref_factors, n, U_gpu):
     return gap, sin_max
 
 
+def contained_sin(T, ref_factors, n, U_gpu, gap_gate=GAP_GATE):
+    """For a large mode whose full rank-r split has no usable gap: the
+    leading k eigenvectors of the mode-n Gram at the oracle's solution, for
+    the largest k with (l_k - l_{r+1}) / l_1 > gap_gate, must lie in the GPU's
+    r-dimensional subspace.  Davis-Kahan on the split (k | beyond r) bounds
+    how far an FP32 operator can move them: sin <~ u l_1 / (l_k - l_{r+1}).
+    Returns (k, largest sine between span(V_k) and span(U_gpu))."""
+    Y = tucker.multi_mode_product(T, ref_factors, skip=n, transpose=True)
+    w, V = np.linalg.eigh(tucker.gram(tucker.unfold(Y, n)))
+    w, V = w[::-1], V[:, ::-1]
+    r = ref_factors[n].shape[1]
+    lr1 = w[r] if r < len(w) else 0.0
+    k = int(np.sum((w[:r] - lr1) / w[0] > gap_gate))
+    if k == 0:
+        return 0, 0.0
+    Vk = V[:, :k]
+    resid = Vk - U_gpu @ (U_gpu.T @ Vk)
+    return k, float(np.linalg.norm(resid, 2))
+
+
 # ---------------------------------------------------------------- colour
 @pytest.mark.parametrize("space,tol", [("ycbcr", 2e-7), ("ipt", 2e-6), ("ycbcr2020cl", 1e-6)])
 @pytest.mark.parametrize("shape", [(64, 48, 6), (37, 23, 3), (8, 1, 1)])
@@ -392,6 +412,13 @@ def test_xga_scene_parity(mes):
         gap, sin_max = gap_and_sin(T, ref.factors, n, Us[n])
         if gap > GAP_GATE:
             assert sin_max < 1e-3, (n, gap, sin_max)
+    # the large modes (r = 256 of 1024, 192 of 768): the gap at r is ~1e-9 of
+    # l_1, below what FP32 resolves, so the gate is on the leading directions
+    # with a usable gap, which must lie inside the GPU's subspace
+    for n in (0, 1):
+        k, sin_k = contained_sin(T, ref.factors, n, Us[n])
+        print(f"xga mode {n}: leading {k} directions with gap > {GAP_GATE}, sin {sin_k:.2e}")
+        assert k >= 8 and sin_k < 1e-3, (n, k, sin_k)
     # the quantiser on the GPU core is bit-exact against the oracle's quantiser
     core = res["core"].cpu().numpy().transpose(3, 2, 1, 0)
     q, sc = mes.quantize_core(res["core"], cfg["ranks"], 16)
@@ -591,3 +618,72 @@ def test_reconstruction_from_the_fit_pass(mes, prec, rprec):
     ref = mes.reconstruct(res["core"], res["factors"], T.shape, cfg["ranks"], precision=rprec)
     torch.cuda.synchronize()
     assert torch.equal(Xh, ref)
+
+
+@pytest.mark.parametrize("name", ["small_64x48", pytest.param("xga_1024x768", marks=pytest.mark.slow)])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_early_sweeps_match_exact_hooi(mes, name, sweeps):
+    """One and two sweeps at DEFAULT options against the oracle's exact HOOI
+    (T-HOSVD start, exact Gram eigenvectors in every update, Eq. 6 to Eq. 8)
+    after the same number of sweeps: relative fit within 1e-5, and the
+    subspaces where the gap allows (full-rank small modes always agree)."""
+    cfg, img = _scene(name)
+    spec = cfg["spec"]
+    dims = (spec.s1, spec.s2, 3, spec.K)
+    X, _ = mes.colour_convert(torch.from_numpy(img).to(DEV), cfg["space"])
+    res = mes.tucker_als(X, dims, cfg["ranks"], max_iters=sweeps, tol=0.0)
+    torch.cuda.synchronize()
+    T = colour.colour_convert(img, cfg["space"])
+    ref = tucker.hooi(T, cfg["ranks"], sweeps, 0.0)
+    fit = float(res["fit"].cpu())
+    print(f"{name} {sweeps} sweep(s): fit {fit:.9f} oracle {ref.fit:.9f} rel {abs(fit - ref.fit) / ref.fit:.2e}")
+    assert int(res["iters"].cpu()) == sweeps
+    assert abs(fit - ref.fit) / ref.fit < 1e-5
+    Us = factors_np(res)
+    for n in range(4):
+        k, sin_k = contained_sin(T, ref.factors, n, Us[n])
+        print(f"  mode {n}: leading {k} directions, sin {sin_k:.2e}")
+        assert sin_k < 1e-3, (n, k, sin_k)
+
+
+@pytest.fixture(scope="module")
+def fhd_oracle():
+    """The FP64 oracle's decomposition of the 1920x1080x3x10 stack (20 sweeps,
+    T-HOSVD start): about half a minute on the host cores."""
+    cfg, img = _scene("fhd_1920x1080")
+    T = colour.colour_convert(img, cfg["space"])
+    ref = tucker.hooi(T, cfg["ranks"], cfg["iters"], 0.0)
+    Xo = tucker.reconstruct(ref.core, ref.factors)
+    return cfg, img, T, ref, tucker.psnr(T, Xo)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,fit_tol,sin_tol,gap_gate,db_tol", [
+    ("fp32", 1e-5, 1e-3, GAP_GATE, 0.01), ("tf32", 1e-4, 1e-2, 1e-3, 0.1), ("bf16", 1e-4, 1e-2, 1e-3, 0.1)])
+def test_fhd_against_the_oracle(mes, fhd_oracle, prec, fit_tol, sin_tol, gap_gate, db_tol):
+    """The benchmark's workload, 1920x1080x3x10 (ranks 384, 256, 3, 10; 20
+    sweeps; default options), in each precision form against the FP64
+    oracle: relative fit, the large-mode subspaces (the oracle's leading
+    directions with a usable gap inside the GPU's subspace) and the PSNR of
+    the reconstructed stack.  FP32 is gated at the plain-method tolerance,
+    the tensor-core forms at the precision-form target (1e-4 in fit)."""
+    cfg, img, T, ref, psnr_o = fhd_oracle
+    spec = cfg["spec"]
+    dims = (spec.s1, spec.s2, 3, spec.K)
+    X, _ = mes.colour_convert(torch.from_numpy(img).to(DEV), cfg["space"])
+    Xh = torch.empty_like(X)
+    res = mes.tucker_als(X, dims, cfg["ranks"], max_iters=cfg["iters"], tol=0.0, precision=prec, reconstruction=Xh)
+    torch.cuda.synchronize()
+    assert int(res["status"].cpu()) == 0
+    fit = float(res["fit"].cpu())
+    dev = abs(fit - ref.fit) / ref.fit
+    Us = factors_np(res)
+    ps = tucker.psnr(T, to_paper(Xh))
+    sins = [contained_sin(T, ref.factors, n, Us[n], gap_gate) for n in (0, 1)]
+    print(f"fhd {prec}: fit {fit:.9f} oracle {ref.fit:.9f} rel dev {dev:.2e}; PSNR {ps:.3f} dB "
+          f"(oracle {psnr_o:.3f}); mode 1 k={sins[0][0]} sin {sins[0][1]:.2e}, mode 2 k={sins[1][0]} "
+          f"sin {sins[1][1]:.2e}")
+    assert dev < fit_tol
+    assert abs(ps - psnr_o) < db_tol
+    for n, (k, sin_k) in enumerate(sins):
+        assert k >= 8 and sin_k < sin_tol, (n, k, sin_k)

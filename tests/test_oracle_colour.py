@@ -77,6 +77,39 @@ def test_ipt_opponent_axes():
     assert yellow[2] > 0.2 and blue[2] < -0.2
 
 
+def test_srgb_to_xyz_matrix_from_primaries_and_d65():
+    # IEC 61966-2-1 builds the matrix from the chromaticities of the sRGB
+    # primaries (x, y) R (0.64, 0.33), G (0.30, 0.60), B (0.15, 0.06) and of
+    # D65 (0.3127, 0.3290): the columns are the primaries' XYZ, scaled so
+    # that R = G = B = 1 gives the white point with Y = 1.  Derived here from
+    # those six numbers alone, it must round to the oracle's 4-digit table
+    # entry by entry (a typo in any fourth digit fails).
+    xyz = lambda x, y: np.array([x / y, 1.0, (1.0 - x - y) / y])
+    P = np.stack([xyz(0.64, 0.33), xyz(0.30, 0.60), xyz(0.15, 0.06)], 1)
+    M = P * np.linalg.solve(P, xyz(0.3127, 0.3290))
+    np.testing.assert_array_equal(np.round(M, 4), colour.M_RGB2XYZ)
+    assert np.abs(M - colour.M_RGB2XYZ).max() < 5e-5
+
+
+def test_lms_matrix_is_normalised_to_d65():
+    # Ebner-Fairchild normalise the Hunt-Pointer-Estevez cone matrix so that
+    # the D65 white (CIE 1931, X = 0.95047, Y = 1, Z = 1.08883) gives equal
+    # cone responses L = M = S = 1; with four published digits each row lands
+    # within 1e-4 of 1 (a fourth-digit typo in a large entry moves it further).
+    lms = colour.M_XYZ2LMS @ np.array([0.95047, 1.0, 1.08883])
+    assert np.abs(lms - 1.0).max() < 1e-4
+    assert colour.M_XYZ2LMS[2, 0] == 0.0 and colour.M_XYZ2LMS[2, 1] == 0.0
+
+
+def test_ipt_matrix_rows_are_achromatic_exact():
+    # The IPT matrix maps equal L'M'S' to I = 1, P = T = 0: the first row sums
+    # to exactly 1, the two opponent rows to exactly 0 (4.4550 - 4.8510 +
+    # 0.3960 and 0.8056 + 0.3572 - 1.1628), so a single-digit typo anywhere in
+    # the matrix breaks one of the sums.
+    np.testing.assert_allclose(colour.M_LMS2IPT.sum(1), [1.0, 0.0, 0.0], rtol=0, atol=1e-12)
+    assert colour.IPT_EXPONENT == 0.43
+
+
 def test_stack_layout():
     # T(x, y, c, k) is channel c of pixel (x, y) of image k, image row-major
     # with x along the row.
