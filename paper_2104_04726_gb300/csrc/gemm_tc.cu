@@ -188,6 +188,80 @@ struct ColWalk {
   }
 };
 
+// Stores one 32-column chunk of a finished accumulator tile (this lane's row
+// m, columns n0 + c0 .. + 31) to C (and C2), or to the split-K workspace.
+// An output whose n index is contiguous goes through the warp's 32 x 33
+// shared tile so that each store instruction writes 32 consecutive n of one
+// row; an output with contiguous m is written directly (lanes = rows).
+__device__ __forceinline__ void store_chunk(const TcArgs& args, const uint32_t (&v)[32], int64_t m0, int64_t n0,
+                                            int b, int split, int wq, int lane, float* tile, int c0) {
+  const int64_t m = m0 + wq * 32 + lane;
+  const bool mok = m < args.M;
+  const int64_t M_lo = args.M_lo, N_lo = args.N_lo;
+  const int64_t mh = m / M_lo, ml = m - mh * M_lo;
+  const int64_t moff = ml * args.c_m + mh * args.c_mh + (int64_t)b * args.c_b;
+  const int64_t moff2 = ml * args.c2_m + mh * args.c2_mh + (int64_t)b * args.c2_b;
+  // val (this lane's row, 32 columns) through the tile: element (row i of
+  // the warp, n = n0 + c0 + lane) at base + row_off_i + col_off(n) with
+  // col_off(n) = (n mod N_lo) * s_n + (n div N_lo) * s_nh
+  auto store_rows = [&](const float (&val)[32], float* base, int64_t row_off, int64_t s_n, int64_t s_nh,
+                        bool acc, bool rnd) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = val[j];
+    __syncwarp();
+    const int64_t n = n0 + c0 + lane;
+    const int64_t nh = n / N_lo, nl = n - nh * N_lo;
+    const int64_t col_off = nl * s_n + nh * s_nh;
+    for (int i = 0; i < 32; ++i) {
+      const int64_t off = __shfl_sync(0xffffffffu, row_off, i);
+      const int64_t mi = m0 + wq * 32 + i;
+      if (mi < args.M && n < args.N) {
+        float* p = base + off + col_off;
+        float x = tile[i * 33 + lane];
+        if (acc) x += *p;
+        if (rnd) x = mes::round_tf32(x);
+        *p = x;
+      }
+    }
+    __syncwarp();
+  };
+  float val[32];
+  if (args.splits > 1) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) val[j] = __uint_as_float(v[j]);
+    const int64_t row_off = (((int64_t)split * args.batch + b) * args.M + m) * args.N;
+    store_rows(val, args.split_ws, row_off, 1, N_lo, false, false);   // col_off = n
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) val[j] = args.alpha * __uint_as_float(v[j]);
+  if (args.c_n == 1) {
+    store_rows(val, args.C, moff, args.c_n, args.c_nh, args.accumulate != 0, args.round_out != 0);
+  } else if (mok) {
+    ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
+#pragma unroll
+    for (int j = 0; j < 32; ++j, cw.next()) {
+      if (n0 + c0 + j >= args.N) continue;
+      float* p = args.C + moff + cw.off;
+      float w = args.accumulate ? *p + val[j] : val[j];
+      if (args.round_out) w = mes::round_tf32(w);
+      *p = w;
+    }
+  }
+  if (args.C2) {
+    if (args.c2_n == 1) {
+      store_rows(val, args.C2, moff2, args.c2_n, args.c2_nh, false, args.round_out != 0);
+    } else if (mok) {
+      ColWalk cw(n0 + c0, N_lo, args.c2_n, args.c2_nh);
+#pragma unroll
+      for (int j = 0; j < 32; ++j, cw.next()) {
+        if (n0 + c0 + j >= args.N) continue;
+        args.C2[moff2 + cw.off] = args.round_out ? mes::round_tf32(val[j]) : val[j];
+      }
+    }
+  }
+}
+
 template <int KIND, int BN, int STAGES>
 struct Cfg {
   static constexpr int A_BYTES = BM * 128;
@@ -344,52 +418,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int64_t M_lo = args.M_lo, N_lo = args.N_lo;
     const int64_t mh = m / M_lo, ml = m - mh * M_lo;
     const int64_t moff = ml * args.c_m + mh * args.c_mh + (int64_t)b * args.c_b;
-    const int64_t moff2 = ml * args.c2_m + mh * args.c2_mh + (int64_t)b * args.c2_b;
     double sq = 0.0;
-    // Rows of this warp are TMEM lanes (one row per thread after tcgen05.ld).
-    // An output whose n index is contiguous goes through a 32 x 33 shared
-    // tile so that each store instruction writes 32 consecutive n of one row;
-    // an output with contiguous m is written directly (lanes = rows).
     float* tile = epi + (warp - 2) * 32 * 33;
-    const bool c_ncontig = args.c_n == 1;
-    const bool c2_ncontig = args.C2 && args.c2_n == 1;
-    // writes val (this lane's row, 32 columns) through the tile: element
-    // (row i of the warp, n = n0 + c0 + lane) at base + row_off_i + col_off(n)
-    // with col_off(n) = (n mod N_lo) * s_n + (n div N_lo) * s_nh
-    auto store_rows = [&](const float (&val)[32], float* base, int64_t row_off, int64_t c0, int64_t s_n,
-                          int64_t s_nh, bool acc, bool rnd) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = val[j];
-      __syncwarp();
-      const int64_t n = n0 + c0 + lane;
-      const int64_t nh = n / N_lo, nl = n - nh * N_lo;
-      const int64_t col_off = nl * s_n + nh * s_nh;
-      for (int i = 0; i < 32; ++i) {
-        const int64_t off = __shfl_sync(0xffffffffu, row_off, i);
-        const int64_t mi = m0 + wq * 32 + i;
-        if (mi < args.M && n < args.N) {
-          float* p = base + off + col_off;
-          float v = tile[i * 33 + lane];
-          if (acc) v += *p;
-          if (rnd) v = mes::round_tf32(v);
-          *p = v;
-        }
-      }
-      __syncwarp();
-    };
     for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
       if (!waited) continue;
-      if (args.splits > 1) {
-        float val[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) val[j] = __uint_as_float(v[j]);
-        const int64_t row_off = (((int64_t)split * args.batch + b) * args.M + m) * args.N;
-        store_rows(val, args.split_ws, row_off, c0, 1, N_lo, false, false);   // col_off = n
-        continue;
-      }
-      if constexpr (RESID) {
+      if (RESID && args.splits == 1) {
         if (!mok) continue;
         // 32 squares summed in FP32 (relative error ~32 * 2^-24 of a
         // non-negative sum), then one FP64 add per chunk: GB300's FP64
@@ -423,36 +458,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         }
         sq += (double)sqf;
         continue;
-      } else {
-        float val[32];
-  #pragma unroll
-        for (int j = 0; j < 32; ++j) val[j] = args.alpha * __uint_as_float(v[j]);
-        if (c_ncontig) {
-          store_rows(val, args.C, moff, c0, args.c_n, args.c_nh, args.accumulate != 0, args.round_out != 0);
-        } else if (mok) {
-          ColWalk cw(n0 + c0, N_lo, args.c_n, args.c_nh);
-  #pragma unroll
-          for (int j = 0; j < 32; ++j, cw.next()) {
-            if (n0 + c0 + j >= args.N) continue;
-            float* p = args.C + moff + cw.off;
-            float w = args.accumulate ? *p + val[j] : val[j];
-            if (args.round_out) w = mes::round_tf32(w);
-            *p = w;
-          }
-        }
-        if (args.C2) {
-          if (c2_ncontig) {
-            store_rows(val, args.C2, moff2, c0, args.c2_n, args.c2_nh, false, args.round_out != 0);
-          } else if (mok) {
-            ColWalk cw(n0 + c0, N_lo, args.c2_n, args.c2_nh);
-  #pragma unroll
-            for (int j = 0; j < 32; ++j, cw.next()) {
-              if (n0 + c0 + j >= args.N) continue;
-              args.C2[moff2 + cw.off] = args.round_out ? mes::round_tf32(val[j]) : val[j];
-            }
-          }
-        }
       }
+      store_chunk(args, v, m0, n0, b, split, wq, lane, tile, c0);
     }
     if (RESID) {
       for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
@@ -471,6 +478,208 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// --------------------------------------------------------------------------
+// Persistent form of the same product (KIND 0 and 1, no residual): one CTA
+// per SM walks the tiles t = blockIdx.x, + gridDim.x, ... (tile index m
+// fastest, then n, batch, split, so the CTAs running side by side share an
+// operand tile through L2).  Two TMEM accumulators of BN columns each: the
+// MMA thread fills accumulator j & 1 for local tile j while the epilogue
+// warps drain the other, and the TMA ring runs ahead across tile
+// boundaries, so loads, MMAs and stores of neighbouring tiles overlap.
+// Barriers: full/empty per ring stage, tfull (accumulator complete, MMA ->
+// epilogue, one commit) and tempty (accumulator drained, epilogue -> MMA,
+// one arrival per epilogue warp) per accumulator.  Every wait is bounded;
+// on a timeout a role sets its error bit and leaves its loop, and the
+// teardown drains loads and MMAs in flight as in tc_gemm_kernel.
+// --------------------------------------------------------------------------
+template <int KIND, int BN, int STAGES>
+struct PCfg {
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int EPI = kEpiWarps * 32 * 33 * 4;   // per-warp transpose tiles (own region)
+  static constexpr int BAR = 8 * (2 * STAGES + 5);
+  static constexpr int SMEM = STAGES * STAGE + EPI + 1024 /*align*/ + BAR + 16;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static constexpr uint32_t FMT = KIND == 1 ? 1u : 2u;
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators: 256 or 512 columns (powers of 2)
+};
+
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const TcArgs args, int mt, int nt, int ntiles) {
+  using C = PCfg<KIND, BN, STAGES>;
+  if (args.skip && *args.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* epi = reinterpret_cast<float*>(ring + STAGES * C::STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + STAGES * C::STAGE + C::EPI);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;     // [2]
+  uint64_t* tempty = tfull + 2;         // [2]
+  uint64_t* drain = tempty + 2;         // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
+  const int mn = mt * nt;
+  // tile t -> (m tile, n tile, batch, split); k range of its split
+  auto decode = [&](int t, int64_t& m0, int64_t& n0, int& b, int& split, int& kb, int& ke) {
+    const int mi = t % mt;
+    const int r = t / mt;
+    const int ni = r % nt;
+    const int bs = r / nt;
+    b = bs % args.batch;
+    split = bs / args.batch;
+    m0 = (int64_t)mi * BM;
+    n0 = (int64_t)ni * BN;
+    kb = split * args.kt_per_split;
+    ke = kb + args.kt_per_split;
+    if (ke > args.k_tiles_total) ke = args.k_tiles_total;
+  };
+  (void)mn;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued = 0, last_phase = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int64_t m0, n0;
+      int b, split, kb, ke;
+      decode(t, m0, n0, b, split, kb, ke);
+      for (int kt = kb; kt < ke; ++kt) {
+        if (!mbar_wait(&empty[stage], phase ^ 1u, wait_ns)) {
+          ok = false;
+          break;
+        }
+        issued |= 1u << stage;
+        last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
+        const int kh = kt / args.k_tiles_lo;
+        const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
+        uint8_t* sa = ring + stage * C::STAGE;
+        mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
+        tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
+        tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (!ok) atomicOr(args.err, 8);
+    for (int s2 = 0; s2 < STAGES; ++s2)
+      if (((issued >> s2) & 1u) && !mbar_wait(&full[s2], (last_phase >> s2) & 1u, kDrainNs))
+        atomicOr(args.err, 64);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      int64_t m0, n0;
+      int b, split, kb, ke;
+      decode(t, m0, n0, b, split, kb, ke);
+      const int acc = j & 1;
+      const uint32_t use = (uint32_t)(j >> 1);
+      // the accumulator's previous tile has been drained by the epilogue
+      if (!mbar_wait(&tempty[acc], (use & 1u) ^ 1u, wait_ns)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      for (int kt = kb; kt < ke; ++kt) {
+        if (!mbar_wait(&full[stage], phase, wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(ring + stage * C::STAGE);
+        const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + C::A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma<KIND>(d, da + 2 * kk, db + 2 * kk, C::IDESC, (kt > kb || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&tfull[acc]);
+    }
+    if (!ok) atomicOr(args.err, 16);
+    // teardown: every MMA issued above is complete before TMEM is freed
+    mma_commit(drain);
+    if (!mbar_wait(drain, 0, kDrainNs)) atomicOr(args.err, 64);
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int wq = warp & 3;                 // TMEM lane quarter = rows wq*32 .. wq*32+31
+    const int half = (warp - 2) >> 2;        // columns half*BN/2 .. (half+1)*BN/2 - 1
+    float* tile = epi + (warp - 2) * 32 * 33;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      int64_t m0, n0;
+      int b, split, kb, ke;
+      decode(t, m0, n0, b, split, kb, ke);
+      const int acc = j & 1;
+      const uint32_t use = (uint32_t)(j >> 1);
+      // warp-uniform: the transposed stores shuffle across the warp
+      const bool waited = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], use & 1u, wait_ns));
+      if (!waited) {
+        if (lane == 0) atomicOr(args.err, 32);
+        break;
+      }
+      tc_fence_after();
+      for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        store_chunk(args, v, m0, n0, b, split, wq, lane, tile, c0);
+      }
+      // this warp's part of the accumulator is read: hand it back to the MMA
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -547,6 +756,22 @@ mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const CUtenso
     tc_gemm_kernel<KIND, BN, STAGES, true><<<grid, kThreads, C::SMEM, st>>>(ma, mb, ma2, mb2, a);
   else
     tc_gemm_kernel<KIND, BN, STAGES, false><<<grid, kThreads, C::SMEM, st>>>(ma, mb, ma2, mb2, a);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+template <int KIND, int BN, int STAGES>
+mes_status launch_tcp(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int mt, int nt, int ntiles,
+                      cudaStream_t st) {
+  using C = PCfg<KIND, BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    MES_CUDA_TRY(cudaFuncSetAttribute(tcp_gemm_kernel<KIND, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C::SMEM));
+    attr = true;
+  }
+  const int grid = ntiles < mes::sm_count() ? ntiles : mes::sm_count();
+  tcp_gemm_kernel<KIND, BN, STAGES><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a, mt, nt, ntiles);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
@@ -643,7 +868,19 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
                    (kind == 1 ? 2.0 : kind == 2 ? 8.0 : 4.0) * g.batch * ((double)g.M + g.N) * g.K_lo * g.K_hi +
                        4.0 * g.batch * g.M * (double)g.N);
     const bool rs = g.ref != nullptr;
-    if (kind == 0) {
+    const int mt = (int)((g.M + BM - 1) / BM), nt = (int)((g.N + bn - 1) / bn);
+    const int64_t ntiles = (int64_t)mt * nt * g.batch * splits;
+    static const bool classic = getenv("MES_TC_CLASSIC") != nullptr;
+    if (kind != 2 && !rs && !g.accumulate && !classic && ntiles < INT32_MAX) {
+      // persistent kernel: tiles looped per CTA, double-buffered accumulator
+      if (kind == 0) {
+        if (bn == 256) MES_TRY((launch_tcp<0, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
+        else MES_TRY((launch_tcp<0, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+      } else {
+        if (bn == 256) MES_TRY((launch_tcp<1, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
+        else MES_TRY((launch_tcp<1, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+      }
+    } else if (kind == 0) {
       if (bn == 256) MES_TRY((launch_tc<0, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
       else MES_TRY((launch_tc<0, 128, 3>(ma, mb, ma2, mb2, a, grid, rs, st)));
     } else if (kind == 1) {
