@@ -49,8 +49,11 @@ def _run(lib, impl, A, B):
     return dC.cpu().numpy()
 
 
+# the last two give every CTA of the persistent kernel several tiles (more
+# tiles than SMs), with ragged M and K, for both tile widths (N = 512 -> 256,
+# N = 384 -> 128 wide tiles), so the accumulator hand-off between tiles runs
 SHAPES = [(128, 128, 32, 1), (256, 256, 128, 1), (200, 300, 100, 1), (384, 512, 1920, 2),
-          (128, 128, 4096, 1), (1000, 72, 648, 3)]
+          (128, 128, 4096, 1), (1000, 72, 648, 3), (8192, 512, 128, 4), (6000, 384, 200, 3)]
 
 
 @pytest.mark.parametrize("M,N,K,batch", SHAPES)
