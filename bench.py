@@ -8,7 +8,7 @@ is stacks per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--precision bf16|tf32|fp32] [--stacks S] [--no-fp32-path]
-                  [--batch-stacks B] [--serve-requests R] [--serve-rate RATE]
+                  [--batch-stacks B] [--serve-seconds S] [--serve-rate RATE]
 
 The default times the BF16 form over 16 concurrent stacks per step and,
 beside it, the plain FP32 path on the same stacks (its stacks/s and the
@@ -135,17 +135,26 @@ def whole_job_rate(stacks_per_rank: int, steps: int, world: int, ms: float) -> f
     return stacks_per_rank * steps * world / (ms / 1e3)
 
 
-def cpu_baseline(sample_sweeps: int = 1):
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+
+
+def cpu_baseline(sample_sweeps: int = 1, workload: str = WORKLOAD):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample
     of the workload: colour pre-pass, T-HOSVD initialisation and
-    `sample_sweeps` HOOI sweeps of one stack, plus the quantiser, timed and
-    scaled to the full 20-sweep decomposition."""
+    `sample_sweeps` HOOI sweeps of one stack, plus the quantiser.  `seconds`
+    is the sample's measured wall time; `stack_seconds` scales the sweep
+    time to the workload's full sweep count (an extrapolation, declared)."""
     import numpy as np
     import synth
     from oracle import colour, quant, tucker
-    cfg = synth.config_spec(WORKLOAD)
+    cfg = synth.config_spec(workload)
     spec = cfg["spec"]
-    img = synth.make_stack(spec, synth.seed_for(WORKLOAD))
+    img = synth.make_stack(spec, synth.seed_for(workload))
     t0 = time.perf_counter()
     T = colour.colour_convert(img, cfg["space"])
     t1 = time.perf_counter()
@@ -156,15 +165,23 @@ def cpu_baseline(sample_sweeps: int = 1):
     quant.quantize_planes(quant.planes_of(res.core.astype(np.float32)), 16)
     t4 = time.perf_counter()
     per_stack = (t1 - t0) + (t2 - t1) + (t3 - t2) * cfg["iters"] / sample_sweeps + (t4 - t3)
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
-    return {"value": 1.0 / per_stack, "unit": "stacks/s", "cores": int(cores), "kind": "oracle",
+    return {"value": 1.0 / per_stack, "unit": "stacks/s", "cores": int(_blas_threads()), "kind": "oracle",
             "sample": (f"1 stack {spec.s1}x{spec.s2}x3x{spec.K}: colour + T-HOSVD + {sample_sweeps} "
-                       f"HOOI sweep(s) + quantiser, sweep time scaled to {cfg['iters']} sweeps"),
-            "seconds": t4 - t0}
+                       f"HOOI sweep(s) + quantiser, the sweep time scaled to {cfg['iters']} sweeps"),
+            "seconds": t4 - t0, "stack_seconds": per_stack, "extrapolated_from_sweeps": sample_sweeps}
+
+
+def oracle_thread_scaling(workload: str = "xga_1024x768"):
+    """Wall time of one oracle sample (colour, T-HOSVD, one sweep,
+    quantiser) on all host cores and on one thread (a child process with
+    the BLAS thread pools limited to 1)."""
+    allc = cpu_baseline(1, workload)["seconds"]
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", workload],
+                       capture_output=True, text=True, env=env, timeout=600)
+    one = float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 and r.stdout.strip() else None
+    return {"sample": f"{workload}: colour + T-HOSVD + 1 HOOI sweep + quantiser", "all_cores_s": allc,
+            "all_cores_threads": int(_blas_threads()), "one_thread_s": one, "host_cores": os.cpu_count()}
 
 
 def _config(name, cfg, dims, ranks, precision, stacks, world):
@@ -176,30 +193,36 @@ def _config(name, cfg, dims, ranks, precision, stacks, world):
 
 
 def run_reference(args):
-    """The oracle timed on the host cores: one bounded sample of the workload
-    per step (rank 0 only)."""
+    """The oracle timed on the host cores (rank 0 only): every step is one
+    bounded sample of the workload (colour, T-HOSVD, one HOOI sweep and the
+    quantiser of one stack).  ms_per_step is the measured time of a sample;
+    the value is stacks/s of the full 20-sweep decomposition, the sample's
+    sweep scaled to 20 sweeps (declared in the line)."""
     import synth
     rank, world, _ = _dist_env()
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_baseline(1)
-    times = []
-    last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(1)
-        times.append(1.0 / last["value"])
-    per = statistics.mean(times)
-    val = 1.0 / per
+        cpu_baseline(1, args.workload)
+    samples = [cpu_baseline(1, args.workload) for _ in range(args.steps)]
+    step_s = statistics.mean(c["seconds"] for c in samples)
+    stack_s = statistics.mean(c["stack_seconds"] for c in samples)
+    val = 1.0 / stack_s
     cfg = synth.config_spec(args.workload)
     spec = cfg["spec"]
+    conf = _config(args.workload, cfg, [spec.s1, spec.s2, 3, spec.K], list(cfg["ranks"]), "f64", 1, world)
+    conf["stacks_per_step"] = step_s / stack_s
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "stacks/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(args.workload, cfg, [spec.s1, spec.s2, 3, spec.K], list(cfg["ranks"]),
-                              args.precision, args.stacks, world),
-            "cpu_baseline": {"value": val, "unit": "stacks/s", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+            "config": conf,
+            "sample_per_step": samples[-1]["sample"],
+            "extrapolated_from_sweeps": 1,
+            "value_note": ("each step times one sample (one sweep of the 20); value = stacks_per_step / "
+                           "seconds per step, i.e. the sample's sweep time scaled to 20 sweeps"),
+            "cpu_baseline": {"value": val, "unit": "stacks/s", "cores": samples[-1]["cores"], "kind": "oracle",
+                             "sample": samples[-1]["sample"]},
+            "thread_scaling": oracle_thread_scaling(),
             "e2e": {"value": val, "unit": "stacks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -257,6 +280,25 @@ def _family_roof(f, peaks, peak_src, sms):
     return roof
 
 
+def algorithmic_flops_per_stack(dims, ranks, sweeps):
+    """Algorithmic flops of the paper's method on one stack: per sweep the
+    two mode products with T (2 N_el (r1 + r2)), the Gram products of the
+    two large unfoldings as symmetric rank-k updates (s1^2 r2 L + s2^2 r1 L)
+    and the core (2 r1 s2 L r2); once, the Gram products of the T-HOSVD
+    start (s1^2 s2 L + s2^2 s1 L).  Small modes at full rank add nothing.
+    The eigen-solver's own iterations are not counted (the paper does not
+    fix one)."""
+    s1, s2 = dims[0], dims[1]
+    r1, r2 = ranks[0], ranks[1]
+    L = 1
+    for d in dims[2:]:
+        L *= d
+    nel = s1 * s2 * L
+    sweep = 2.0 * nel * (r1 + r2) + s1 * s1 * r2 * L + s2 * s2 * r1 * L + 2.0 * r1 * s2 * L * r2
+    init = float(s1) * s1 * s2 * L + float(s2) * s2 * s1 * L
+    return sweeps * sweep + init
+
+
 def _roofline(fams, peaks, peak_src, sms):
     total_ms = sum(f["ms"] for f in fams) or 1.0
     top = fams[0]
@@ -289,98 +331,145 @@ def _family_rooflines(fams, peaks, peak_src, sms, n=6):
 SERVE_SIZES = ((640, 480), (1280, 720), (1920, 1080))
 
 
-def measure_serving(mes, dev, precision, n_req, rate, seed, slots, budget_gb):
-    """Serving form: a Poisson request stream (`rate` per second, `n_req`
-    requests) of stacks drawn like the mixed workload -- 640x480, 1280x720 or
-    1920x1080 with 3..7 exposures per view, or 3840x2160 with 3 exposures at
-    5% -- ranks 20% of the two image modes (full rank for colour and
-    view x exposure), IPT or Y'CbCr at random, 20 sweeps, 16-bit quantised
-    core.  Requests are submitted at their arrival times to the library's
-    serving loop (continuous batching under a device-memory budget); latency
-    is submission to completion.  Beside it, one request of each size through
-    the plain FP32 path alone on one stream."""
-    import numpy as np
+def _serve_mix(mes, dev, seed_base):
+    """The mixed request workload of the serving form: 640x480, 1280x720 or
+    1920x1080 with 3..7 exposures per view, or (5%) 3840x2160 with 3 per
+    view; ranks 20% of the two image modes, full rank for colour and
+    view x exposure; IPT or Y'CbCr.  Returns (scenes, draw(rng))."""
     import torch
     import synth
-
-    rng = np.random.default_rng(seed)
     stops = tuple(2.0 ** e for e in (-3, -2, -1, 0, 1, 2, 3))
     scenes = {}
     for s1, s2 in SERVE_SIZES:
         spec = synth.SceneSpec(s1, s2, stops, views=2, d_max=max(4, s1 // 40))
-        scenes[(s1, s2)] = torch.from_numpy(synth.make_stack(spec, 5000 + s1)).to(dev)
+        scenes[(s1, s2)] = torch.from_numpy(synth.make_stack(spec, seed_base + s1)).to(dev)
     spec4k = synth.SceneSpec(3840, 2160, (0.25, 1.0, 4.0), views=2, d_max=96)
-    scenes[(3840, 2160)] = torch.from_numpy(synth.make_stack(spec4k, 5999)).to(dev)
+    scenes[(3840, 2160)] = torch.from_numpy(synth.make_stack(spec4k, seed_base + 999)).to(dev)
+    inputs = {}
 
-    def draw():
+    def draw(rng):
         if rng.random() < 0.05:
             s1, s2, E = 3840, 2160, 3
         else:
             s1, s2 = SERVE_SIZES[int(rng.integers(3))]
             E = int(rng.integers(3, 8))
-        base = scenes[(s1, s2)]
-        Eb = base.shape[0] // 2
-        rgb = torch.cat([base[:E], base[Eb:Eb + E]]).contiguous()   # view-major, first E exposures
-        dims = (s1, s2, 3, 2 * E)
-        ranks = (round(0.2 * s1), round(0.2 * s2), 3, 2 * E)
+        key = (s1, s2, E)
+        if key not in inputs:   # view-major: the first E exposures of each view
+            base = scenes[(s1, s2)]
+            Eb = base.shape[0] // 2
+            inputs[key] = torch.cat([base[:E], base[Eb:Eb + E]]).contiguous()
         space = "ipt" if rng.random() < 0.5 else "ycbcr"
-        return dims, ranks, rgb, space
+        return key, space
 
-    def problem(d, prec):
-        dims, ranks, rgb, space = d
-        return mes.Problem(dims, ranks, rgb8=rgb, space=space, max_iters=20, tol=0.0, precision=prec,
-                           quant_bits=16)
+    return inputs, draw
 
-    reqs = [draw() for _ in range(n_req)]
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    probs = [problem(d, precision) for d in reqs]
-    # warm-up: one request of each size through the server (one-time setup)
-    srv = mes.Server(int(budget_gb * 2 ** 30), slots)
-    for d in {(r[0][0], r[0][1]): r for r in reqs}.values():
-        w = problem(d, precision)
-        srv.wait(srv.submit(w))
-    srv.close()
-    torch.cuda.synchronize()
-    srv = mes.Server(int(budget_gb * 2 ** 30), slots)
-    t0 = time.perf_counter()
-    tickets = []
-    for a, p in zip(arrivals, probs):
-        dt = t0 + a - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(srv.submit(p))
-    lat, bad = [], 0
-    for t in tickets:
-        st, ms = srv.wait(t)
-        if st == 0:
-            lat.append(ms)
+
+def _serve_run(mes, srv, precision, inputs, draws, arrivals, window, pool):
+    """Submits draws[i] at arrivals[i] seconds (host clock) and collects the
+    latency of every request; completed requests give their buffers back to
+    the pool (keyed by size and exposure count), so memory follows the
+    number of requests outstanding.  Returns per-request latencies (ms),
+    statuses and the wall time."""
+    import time as _t
+    out = {}
+    pending = {}
+
+    def recycle():
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                key, p, i = pending.pop(t)
+                out[i] = r
+                pool.setdefault((key, precision), []).append(p)
+
+    t0 = _t.perf_counter()
+    for i, ((key, space), a) in enumerate(zip(draws, arrivals)):
+        while True:
+            recycle()
+            dt = t0 + a - _t.perf_counter()
+            if dt <= 0:
+                break
+            _t.sleep(min(dt, 0.002))
+        free = pool.get((key, precision))
+        if free:
+            p = free.pop()
         else:
-            bad += 1
-    wall = time.perf_counter() - t0
-    stats = srv.stats()
-    srv.close()
-    eq = sum(d[0][0] * d[0][1] * d[0][3] for d in reqs) / (1920 * 1080 * 10)
-    fits = [float(p.fit) for p in probs]
-    # plain FP32 path, one request of each size alone on one stream
-    fp32 = {}
-    for d in {(r[0][0], r[0][1]): r for r in reqs}.values():
-        p = problem(d, "fp32")
-        torch.cuda.synchronize()
-        a0 = time.perf_counter()
-        b = mes.Batch(1)
-        b.run([p])
-        torch.cuda.synchronize()
-        fp32[f"{d[0][0]}x{d[0][1]}x3x{d[0][3]}"] = round(1e3 * (time.perf_counter() - a0), 2)
-        b.close()
-    lat_np = np.array(lat) if lat else np.array([float("nan")])
-    return {"requests": n_req, "rate_per_s": rate, "completed": len(lat), "failed": bad, "precision": precision,
-            "slots": slots, "hbm_budget_gib": budget_gb,
-            "p50_ms": float(np.percentile(lat_np, 50)), "p99_ms": float(np.percentile(lat_np, 99)),
-            "max_ms": float(lat_np.max()), "stacks_per_s": len(lat) / wall,
-            "fhd_equiv_stacks_per_s": eq / wall, "offered_fhd_equiv_per_s": eq / arrivals[-1],
-            "wall_s": wall, "hbm_peak_gib": stats["hbm_peak"] / 2 ** 30,
-            "all_fits_finite": bool(all(np.isfinite(fits))),
-            "fp32_alone_ms": fp32}
+            s1, s2, E = key
+            p = mes.Problem((s1, s2, 3, 2 * E), (round(0.2 * s1), round(0.2 * s2), 3, 2 * E), rgb8=inputs[key],
+                            space=space, max_iters=20, tol=0.0, precision=precision, quant_bits=16)
+        p.struct.space = mes.SPACES[space]
+        pending[srv.submit(p)] = (key, p, i)
+    while pending:
+        recycle()
+        _t.sleep(0.0005)
+    wall = _t.perf_counter() - t0
+    lat = [out[i][1] for i in range(len(draws))]
+    st = [out[i][0] for i in range(len(draws))]
+    return lat, st, wall
+
+
+def measure_serving(mes, dev, precision, rate_cap, seconds, warm_s, fp32_seconds, seed, slots, budget_gb):
+    """Serving form as the serving workload defines it: Poisson arrivals of
+    the mixed requests (20 sweeps, 16-bit quantised core) into the library's
+    serving loop (continuous batching under a device-memory budget), warm_s
+    seconds of warm-up then `seconds` measured; latency is submission to
+    observed completion.  The arrival rate is rate_cap (200/s) or 80% of the
+    measured capacity when that is lower (above capacity the queue, and with
+    it every latency, grows without bound).  Capacity = a burst of requests
+    submitted at once, completions per second.  Beside it the plain
+    per-request FP32 path served the same way: FP32 precision, one slot (one
+    request at a time on one stream), at 80% of its own capacity."""
+    import numpy as np
+    import torch
+
+    inputs, draw = _serve_mix(mes, dev, 5000)
+    pool = {}
+
+    def arm(prec, nslots, secs):
+        rng = np.random.default_rng(seed)
+        srv = mes.Server(int(budget_gb * 2 ** 30), nslots)
+        try:
+            # one request of every size first: one-time setup outside the measurement
+            seen = set()
+            warm = []
+            for _ in range(200):
+                d = draw(rng)
+                if d[0] not in seen:
+                    seen.add(d[0])
+                    warm.append(d)
+            _serve_run(mes, srv, prec, inputs, warm, [0.0] * len(warm), None, pool)
+            burst = [draw(rng) for _ in range(6 * nslots + 8)]
+            lat, st, wall = _serve_run(mes, srv, prec, inputs, burst, [0.0] * len(burst), None, pool)
+            capacity = len(burst) / wall
+            rate = min(rate_cap, 0.8 * capacity)
+            n = int(rate * (warm_s + secs)) + 1
+            draws = [draw(rng) for _ in range(n)]
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            lat, st, wall = _serve_run(mes, srv, prec, inputs, draws, arrivals, None, pool)
+            meas = [i for i in range(n) if warm_s <= arrivals[i] < warm_s + secs]
+            lm = np.array([lat[i] for i in meas if st[i] == 0]) if meas else np.array([float("nan")])
+            eq = sum(draws[i][0][0] * draws[i][0][1] * 2 * draws[i][0][2] for i in meas) / (1920 * 1080 * 10)
+            stats = srv.stats()
+        finally:
+            srv.close()
+        return {"precision": prec, "slots": nslots, "capacity_req_per_s": capacity, "rate_per_s": rate,
+                "warmup_s": warm_s, "measured_s": secs, "requests_measured": len(meas),
+                "failed": int(sum(1 for i in meas if st[i] != 0)),
+                "p50_ms": float(np.percentile(lm, 50)), "p99_ms": float(np.percentile(lm, 99)),
+                "max_ms": float(lm.max()), "stacks_per_s": len(meas) / secs,
+                "fhd_equiv_stacks_per_s": eq / secs, "hbm_peak_gib": stats["hbm_peak"] / 2 ** 30}
+
+    served = arm(precision, slots, seconds)
+    torch.cuda.synchronize()
+    plain = arm("fp32", 1, fp32_seconds) if fp32_seconds > 0 else None
+    pool.clear()
+    torch.cuda.synchronize()
+    out = dict(served)
+    out.update({"hbm_budget_gib": budget_gb, "rate_cap_per_s": rate_cap,
+                "rate_note": ("the workload's 200/s exceeds the measured capacity: run at 80% of capacity"
+                              if served["rate_per_s"] < rate_cap else "run at the workload's rate"),
+                "fp32_per_request_arm": plain})
+    return out
 
 
 def measure_batch(mes, dev, precision, n_stacks, seed):
@@ -466,12 +555,20 @@ def main():
                     help="skip timing the plain FP32 path beside the chosen precision form")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--stacks", type=int, default=16, help="independent stacks per step, one CUDA stream each")
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests of the serving measurement (0 = skip it)")
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="measured seconds of the serving form (0 = skip it)")
+    ap.add_argument("--serve-warmup", type=float, default=10.0, help="warm-up seconds before the measured window")
+    ap.add_argument("--serve-fp32-seconds", type=float, default=30.0,
+                    help="measured seconds of the plain per-request FP32 served arm (0 = skip it)")
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="Poisson arrival rate of the serving form (capped at 80%% of the measured capacity)")
     ap.add_argument("--batch-stacks", type=int, default=64,
                     help="stacks of the batched-form measurement (0 = skip it)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:
+        print(cpu_baseline(1, args.oracle_sample)["seconds"])
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
@@ -608,11 +705,14 @@ def main():
                "fit": fits[0], "fits": fits}
         if not detail:
             return out
-        # per-kernel profile over K more steps (events on each launch stream)
+        # per-kernel profile: two stacks one after the other (events on the
+        # launch stream, nothing else running), so every interval is the
+        # kernel's own serialised duration, as in an ncu launch list
+        prof_stacks = min(2, S)
         lib.mes_profile_enable(1)
-        for _ in range(args.steps):
-            step(precision)
-        torch.cuda.synchronize()
+        for st_ in stacks[:prof_stacks]:
+            st_.run(precision)
+            torch.cuda.synchronize()
         fams = []
         for i in range(lib.mes_profile_count()):
             nm = ctypes.create_string_buffer(64)
@@ -625,7 +725,8 @@ def main():
         lib.mes_profile_enable(0)
         fams.sort(key=lambda f: -f["ms"])
         out["fams"] = fams
-        out["launches_per_step"] = sum(f["launches"] for f in fams) // args.steps
+        out["launches_per_step"] = S * sum(f["launches"] for f in fams) // prof_stacks
+        out["prof_stacks"] = prof_stacks
         # end to end through the public API with host buffers
         step(precision, True)
         torch.cuda.synchronize()
@@ -641,6 +742,13 @@ def main():
     peaks, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     roof = _roofline(res["fams"], peaks, peak_src, sms)
+    flops_stack = algorithmic_flops_per_stack(dims, ranks, iters)
+    step_tf = flops_stack * S / (res["ms_per_step"] / 1e3) / 1e12
+    step_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    step_roof = {"bound": "tensor", "achieved": step_tf, "peak": step_peak, "unit": "TFLOP/s",
+                 "frac": step_tf / step_peak, "algorithmic_flops_per_stack": flops_stack,
+                 "note": (f"whole step: algorithmic flops of the method per stack x {S} stacks / ms_per_step, "
+                          f"against the {peak_src} sustained BF16 peak")}
     h2d = S * stacks[0].rgb_host.numel()
     d2h = S * (stacks[0].q_host.numel() * 2 + P * 4 + sum(f.numel() * 4 for f in stacks[0].f_host) + 8)
     if rank == 0:
@@ -652,6 +760,10 @@ def main():
                                launch="value: the step captured once as a CUDA graph and replayed; "
                                       "e2e: eager API calls"),
                 "roofline": roof, "rooflines": _family_rooflines(res["fams"], peaks, peak_src, sms),
+                "rooflines_note": (f"per kernel family from a profiled pass of {res['prof_stacks']} stacks run one "
+                                   "after another (CUDA events on the launch stream, no other work on the GPU): "
+                                   "serialised durations and shares, as in an ncu launch list"),
+                "step_roofline": step_roof,
                 "gpu_launches": int(res["launches_per_step"] * args.steps),
                 "clocks": res["clocks"],
                 "e2e": {"value": res["e2e"], "unit": "stacks/s", "h2d_bytes_per_step": int(h2d),
@@ -666,9 +778,10 @@ def main():
                                  "clocks": fp32["clocks"]}
         if args.batch_stacks > 0 and world == 1:
             line["batch"] = measure_batch(mes, dev, args.precision, args.batch_stacks, seed=11)
-        if args.serve_requests > 0 and world == 1:
-            line["serve"] = measure_serving(mes, dev, args.precision, args.serve_requests, args.serve_rate,
-                                            seed=7, slots=8, budget_gb=96)
+        if args.serve_seconds > 0 and world == 1:
+            line["serve"] = measure_serving(mes, dev, args.precision, args.serve_rate, args.serve_seconds,
+                                            args.serve_warmup, args.serve_fp32_seconds, seed=7, slots=8,
+                                            budget_gb=96)
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
