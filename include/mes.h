@@ -454,7 +454,9 @@ mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, d
  * C[b][m][n] = sum_k A[b][m][k] * B[b][n][k], all row-major FP32 device
  * arrays, batch >= 1.  impl 0: CUDA-core FP32 kernel; 1: tcgen05 kind::tf32;
  * 2: tcgen05 kind::f16 on BF16-rounded copies of A and B; 3: tcgen05
- * kind::tf32 on the three-term split (hi + lo of A and B).  Synchronises the
+ * kind::tf32 on the three-term split (hi + lo of A and B); 4: tcgen05
+ * kind::f16 on the six-term split (three BF16 parts of A and B, the six
+ * part products down to 2^-16 of the leading one).  Synchronises the
  * stream.  MES_ERR_INVALID_ARG for bad sizes or operands the tensor-core
  * kernel cannot address (row strides must be multiples of 16 bytes);
  * MES_ERR_TIMEOUT if a bounded pipeline wait gave up.

@@ -16,7 +16,13 @@
 // three-term TF32 split (KIND 2): with A = A_hi + A_lo and B = B_hi + B_lo,
 // both terms exactly TF32, each K slice issues A_hi B_hi + A_hi B_lo +
 // A_lo B_hi into one accumulator (the dropped A_lo B_lo is ~2^-22 of the
-// product), so the result has FP32-level accuracy.  Split-K over
+// product), so the result has FP32-level accuracy.  KIND 3, the six-term
+// BF16 split: each operand is stored as three BF16 parts x = x1 + x2 + x3
+// (24 significant bits, as many as FP32) in the K_hi planes of its tensor
+// map, and the K walk runs over the part pairs (1,1) (1,2) (2,1) (1,3) (3,1)
+// (2,2) -- every product down to 2^-16 of the leading one -- into one FP32
+// accumulator, so the result has FP32-level accuracy at BF16 tensor-core
+// rate (used for the Grams of the factor update).  Split-K over
 // grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
 // result is deterministic.  Every mbarrier wait is bounded (globaltimer,
 // 2 s unless the caller sets a shorter bound); a timeout sets an error bit.
@@ -64,7 +70,14 @@ struct TcArgs {
   const int* skip;
   int* err;
   uint64_t wait_ns;    // bound of each pipeline wait (0: kWaitNs)
+  int lower;           // skip tiles wholly above the diagonal (n0 >= m0 + BM)
 };
+
+// Element bytes of an operand kind: BF16 for kinds 1 and 3, FP32 otherwise.
+__host__ __device__ constexpr int kind_bytes(int kind) { return (kind == 1 || kind == 3) ? 2 : 4; }
+// KIND 3: operand part of pair q (0..5) for A and for B.
+__device__ __forceinline__ int pair_a(int q) { return (0x120100 >> (4 * q)) & 0xF; }   // 0,0,1,0,2,1
+__device__ __forceinline__ int pair_b(int q) { return (0x102010 >> (4 * q)) & 0xF; }   // 0,1,0,2,0,1
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -135,7 +148,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (KIND != 1) {
+  if (KIND != 1 && KIND != 3) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
@@ -350,7 +363,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
       const int kt = kt_begin + i;
       const int kh = kt / args.k_tiles_lo;
-      const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
+      const int kl = (kt - kh * args.k_tiles_lo) * (128 / kind_bytes(KIND));
       uint8_t* sa = tiles + stage * C::STAGE;
       mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
       tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
@@ -504,7 +517,7 @@ struct PCfg {
   static constexpr int BAR = 8 * (2 * STAGES + 5);
   static constexpr int SMEM = STAGES * STAGE + EPI + 1024 /*align*/ + BAR + 16;
   static_assert(SMEM <= 232448, "shared memory per CTA");
-  static constexpr uint32_t FMT = KIND == 1 ? 1u : 2u;
+  static constexpr uint32_t FMT = (KIND == 1 || KIND == 3) ? 1u : 2u;
   static constexpr uint32_t IDESC =
       (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators: 256 or 512 columns (powers of 2)
@@ -554,7 +567,9 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const uint64_t wait_ns = args.wait_ns ? args.wait_ns : kWaitNs;
   const int mn = mt * nt;
   // tile t -> (m tile, n tile, batch, split); k range of its split
-  auto decode = [&](int t, int64_t& m0, int64_t& n0, int& b, int& split, int& kb, int& ke) {
+  // (false: a tile wholly above the diagonal of a lower-only product; every
+  // role skips the same tiles)
+  auto decode = [&](int t, int64_t& m0, int64_t& n0, int& b, int& split, int& kb, int& ke) -> bool {
     const int mi = t % mt;
     const int r = t / mt;
     const int ni = r % nt;
@@ -566,6 +581,7 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     kb = split * args.kt_per_split;
     ke = kb + args.kt_per_split;
     if (ke > args.k_tiles_total) ke = args.k_tiles_total;
+    return !(args.lower && n0 >= m0 + BM);
   };
   (void)mn;
 
@@ -578,7 +594,7 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int64_t m0, n0;
       int b, split, kb, ke;
-      decode(t, m0, n0, b, split, kb, ke);
+      if (!decode(t, m0, n0, b, split, kb, ke)) continue;
       for (int kt = kb; kt < ke; ++kt) {
         if (!mbar_wait(&empty[stage], phase ^ 1u, wait_ns)) {
           ok = false;
@@ -587,11 +603,13 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         issued |= 1u << stage;
         last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
         const int kh = kt / args.k_tiles_lo;
-        const int kl = (kt - kh * args.k_tiles_lo) * (128 / (KIND == 1 ? 2 : 4));
+        const int kl = (kt - kh * args.k_tiles_lo) * (128 / kind_bytes(KIND));
+        // KIND 3: K block kh is part pair kh; the parts are the K_hi planes
+        const int kha = KIND == 3 ? pair_a(kh) : kh, khb = KIND == 3 ? pair_b(kh) : kh;
         uint8_t* sa = ring + stage * C::STAGE;
         mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
-        tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
-        tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+        tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kha, args.a_batched ? b : 0);
+        tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, khb, args.b_batched ? b : 0);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
@@ -608,10 +626,10 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     uint32_t phase = 0;
     bool ok = true;
     int j = 0;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int64_t m0, n0;
       int b, split, kb, ke;
-      decode(t, m0, n0, b, split, kb, ke);
+      if (!decode(t, m0, n0, b, split, kb, ke)) continue;
       const int acc = j & 1;
       const uint32_t use = (uint32_t)(j >> 1);
       // the accumulator's previous tile has been drained by the epilogue
@@ -640,6 +658,7 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       if (!ok) break;
       mma_commit(&tfull[acc]);
+      ++j;
     }
     if (!ok) atomicOr(args.err, 16);
     // teardown: every MMA issued above is complete before TMEM is freed
@@ -651,10 +670,10 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int half = (warp - 2) >> 2;        // columns half*BN/2 .. (half+1)*BN/2 - 1
     float* tile = epi + (warp - 2) * 32 * 33;
     int j = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       int64_t m0, n0;
       int b, split, kb, ke;
-      decode(t, m0, n0, b, split, kb, ke);
+      if (!decode(t, m0, n0, b, split, kb, ke)) continue;
       const int acc = j & 1;
       const uint32_t use = (uint32_t)(j >> 1);
       // warp-uniform: the transposed stores shuffle across the warp
@@ -673,6 +692,7 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       tc_fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+      ++j;
     }
   }
   tc_fence_before();
@@ -693,6 +713,7 @@ __global__ void split_reduce_kernel(const float* __restrict__ ws, TcArgs a) {
     const int64_t n = e % a.N;
     const int64_t bm = e / a.N;
     const int64_t m = bm % a.M, b = bm / a.M;
+    if (a.lower && n > m) continue;   // the consumer reads the lower triangle only
     const int64_t mh = m / a.M_lo, ml = m - mh * a.M_lo, nh = n / a.N_lo, nl = n - nh * a.N_lo;
     float val = a.alpha * s;
     float* p = a.C + ml * a.c_m + mh * a.c_mh + nl * a.c_n + nh * a.c_nh + b * a.c_b;
@@ -721,7 +742,7 @@ mes_status get_encode() {
 // 4-D map {K_lo, rows, K_hi, batch} of a K-major operand.
 bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_t rows, int64_t K_hi,
               int64_t batch, int64_t s_row, int64_t s_kh, int64_t s_b, int box_rows) {
-  const int E = kind == 1 ? 2 : 4;
+  const int E = kind_bytes(kind);
   cuuint64_t dims[4] = {(cuuint64_t)K_lo, (cuuint64_t)rows, (cuuint64_t)K_hi, (cuuint64_t)batch};
   int64_t st[3] = {s_row * E, s_kh * E, s_b * E};
   // unit dims get a harmless stride that keeps the strides increasing
@@ -733,7 +754,7 @@ bool make_map(CUtensorMap* map, const void* base, int kind, int64_t K_lo, int64_
   cuuint64_t strides[3] = {(cuuint64_t)st[0], (cuuint64_t)st[1], (cuuint64_t)st[2]};
   cuuint32_t box[4] = {(cuuint32_t)(128 / E), (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(map, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+  CUresult r = g_encode(map, E == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -781,7 +802,7 @@ mes_status launch_tcp(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs
 namespace mes {
 
 bool tc_eligible(const Gemm& g, int kind) {
-  const int E = kind == 1 ? 2 : 4;
+  const int E = kind_bytes(kind);
   if (kind == 2 && (!g.A2 || !g.B2 || reinterpret_cast<uintptr_t>(g.A2) % 16 || reinterpret_cast<uintptr_t>(g.B2) % 16))
     return false;
   if (g.a_k != 1 || g.b_k != 1) return false;
@@ -804,7 +825,7 @@ namespace {
 mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, float* split_ws,
                        int64_t split_ws_elems, int* err, cudaStream_t st) {
   using namespace mes;
-  const int BK = 128 / (kind == 1 ? 2 : 4);
+  const int BK = 128 / kind_bytes(kind);
   if (kind == 2 || (bn != 128 && bn != 256)) bn = 128;   // KIND 2 has only the 128-wide tile
   CUtensorMap ma, mb, ma2, mb2;
   const bool ab = g.batch > 1 && g.a_b != 0, bb = g.batch > 1 && g.b_b != 0;
@@ -823,7 +844,10 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   a.M = g.M;
   a.N = g.N;
   a.k_tiles_lo = (int)((g.K_lo + BK - 1) / BK);
-  a.k_tiles_total = a.k_tiles_lo * (int)g.K_hi;
+  // KIND 3: the K_hi planes are the three parts and the walk runs over six
+  // part pairs
+  a.k_tiles_total = a.k_tiles_lo * (kind == 3 ? 6 : (int)g.K_hi);
+  a.lower = g.lower ? 1 : 0;
   a.batch = g.batch;
   a.a_batched = ab ? 1 : 0;
   a.b_batched = bb ? 1 : 0;
@@ -863,22 +887,29 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   {
     // algorithmic work of the product itself (KIND 2 executes three MMAs
     // per K slice and reads both parts of each operand)
-    ProfScope prof(kind == 0 ? "gemm_tf32_tc" : kind == 1 ? "gemm_bf16_tc" : "gemm_tf32x3_tc", st,
-                   2.0 * g.M * g.N * (double)g.K_lo * g.K_hi * g.batch,
-                   (kind == 1 ? 2.0 : kind == 2 ? 8.0 : 4.0) * g.batch * ((double)g.M + g.N) * g.K_lo * g.K_hi +
+    const double kk = (double)g.K_lo * (kind == 3 ? 1.0 : (double)g.K_hi);   // K of the product itself
+    ProfScope prof(kind == 0 ? "gemm_tf32_tc" : kind == 1 ? "gemm_bf16_tc" : kind == 2 ? "gemm_tf32x3_tc"
+                                                                                    : "gemm_bf16x6_tc",
+                   st, 2.0 * g.M * g.N * kk * g.batch,
+                   (kind == 1 ? 2.0 : kind == 2 ? 8.0 : kind == 3 ? 6.0 : 4.0) * g.batch * ((double)g.M + g.N) * kk +
                        4.0 * g.batch * g.M * (double)g.N);
     const bool rs = g.ref != nullptr;
     const int mt = (int)((g.M + BM - 1) / BM), nt = (int)((g.N + bn - 1) / bn);
     const int64_t ntiles = (int64_t)mt * nt * g.batch * splits;
     static const bool classic = getenv("MES_TC_CLASSIC") != nullptr;
-    if (kind != 2 && !rs && !g.accumulate && !classic && ntiles < INT32_MAX) {
+    if (kind == 3 && (rs || g.accumulate || ntiles >= INT32_MAX))
+      return fail(MES_ERR_INVALID_ARG, "gemm_tc: the six-term product has no residual or accumulate mode");
+    if (kind == 3 || (kind != 2 && !rs && !g.accumulate && !classic && ntiles < INT32_MAX)) {
       // persistent kernel: tiles looped per CTA, double-buffered accumulator
       if (kind == 0) {
         if (bn == 256) MES_TRY((launch_tcp<0, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
         else MES_TRY((launch_tcp<0, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
-      } else {
+      } else if (kind == 1) {
         if (bn == 256) MES_TRY((launch_tcp<1, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
         else MES_TRY((launch_tcp<1, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+      } else {
+        if (bn == 256) MES_TRY((launch_tcp<3, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
+        else MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
       }
     } else if (kind == 0) {
       if (bn == 256) MES_TRY((launch_tc<0, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
@@ -971,8 +1002,8 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
     return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
   }
   // candidates: both tile widths (one for KIND 2) x split-K 1..16 (>= 4 K-tiles a split)
-  const int BK = 128 / (kind == 1 ? 2 : 4);
-  const int64_t kt = ((g.K_lo + BK - 1) / BK) * g.K_hi;
+  const int BK = 128 / kind_bytes(kind);
+  const int64_t kt = ((g.K_lo + BK - 1) / BK) * (kind == 3 ? 6 : g.K_hi);
   cudaEvent_t e0, e1;
   MES_CUDA_TRY(cudaEventCreate(&e0));
   MES_CUDA_TRY(cudaEventCreate(&e1));
@@ -1031,7 +1062,40 @@ __global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16_raw* 
   }
 }
 
+// x -> three BF16 parts x1 = bf(x), x2 = bf(x - x1), x3 = bf(x - x1 - x2)
+// (round to nearest even each; both differences are exact in FP32), written
+// to out[i], out[plane + i], out[2 plane + i].
+__global__ void split_bf16x3_kernel(const float* __restrict__ in, uint16_t* __restrict__ out, int64_t n,
+                                    int64_t plane, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = in[i];
+    const uint16_t b1 = mes::bf16_bits(x);
+    const float r1 = x - __uint_as_float((uint32_t)b1 << 16);
+    const uint16_t b2 = mes::bf16_bits(r1);
+    const float r2 = r1 - __uint_as_float((uint32_t)b2 << 16);
+    out[i] = b1;
+    out[plane + i] = b2;
+    out[2 * plane + i] = mes::bf16_bits(r2);
+  }
+}
+
 }  // namespace
+
+namespace mes {
+
+mes_status split_bf16x3(const float* in, uint16_t* out, int64_t n, int64_t plane, const int* skip,
+                        cudaStream_t st) {
+  if (n <= 0) return MES_OK;
+  MES_TRY(audit(in, (size_t)n * 4 - 1, "split_bf16x3 in"));
+  MES_TRY(audit(out, (size_t)(2 * plane + n) * 2 - 1, "split_bf16x3 out"));
+  ProfScope prof("split_bf16x3", st, 0.0, 10.0 * n);
+  split_bf16x3_kernel<<<grid_for(n, 256, (int64_t)sm_count() * 8), 256, 0, st>>>(in, out, n, plane, skip);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+}  // namespace mes
 
 // Test hook: C[m*N + n] = sum_k A[m*K + k] * B[n*K + k] (both row-major,
 // K-major), through the CUDA-core kernel (impl 0), kind::tf32 (impl 1),
@@ -1040,7 +1104,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16_raw* 
 extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M,
                                         int64_t N, int64_t K, int batch, void* stream) {
   mes::clear_error();
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 3)
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || impl < 0 || impl > 4)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_gemm_selftest: bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
@@ -1081,7 +1145,20 @@ extern "C" mes_status mes_gemm_selftest(int impl, const float* A, const float* B
     g.A = Ah; g.A2 = Al;
     g.B = Bh; g.B2 = Bl;
   }
-  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : impl == 2 ? 1 : 2, ws, ws_elems, err, st));
+  if (impl == 4) {
+    // three BF16 parts of each operand as the K_hi planes (part stride = the operand's size)
+    // layout [batch][part][rows][K]: part stride rows*K, batch stride 3*rows*K
+    uint16_t *Ap, *Bp;
+    MES_TRY(scr.alloc(&Ap, 3 * batch * M * K));
+    MES_TRY(scr.alloc(&Bp, 3 * batch * N * K));
+    for (int b = 0; b < batch; ++b) {
+      MES_TRY(mes::split_bf16x3(A + b * M * K, Ap + 3 * b * M * K, M * K, M * K, nullptr, st));
+      MES_TRY(mes::split_bf16x3(B + b * N * K, Bp + 3 * b * N * K, N * K, N * K, nullptr, st));
+    }
+    g.A = reinterpret_cast<const float*>(Ap); g.K_hi = 3; g.a_kh = M * K; g.a_b = 3 * M * K;
+    g.B = reinterpret_cast<const float*>(Bp); g.b_kh = N * K; g.b_b = 3 * N * K;
+  }
+  MES_TRY(mes::gemm_tc(g, impl == 1 ? 0 : impl == 2 ? 1 : impl == 3 ? 2 : 3, ws, ws_elems, err, st));
   int herr = 0;
   MES_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   MES_CUDA_TRY(cudaStreamSynchronize(st));

@@ -123,6 +123,7 @@ struct Driver {
   float* split_ws = nullptr;
   int64_t split_elems = 0;
   uint16_t* Zh16 = nullptr;                 // BF16 copy of Zh (BF16 form, T-side steps)
+  uint16_t* gparts = nullptr;               // three BF16 parts of a Gram operand (tensor-core forms)
 
   // tensor-core forms: operands of the Y-side products stored TF32-rounded
   bool tc() const { return prec != MES_PREC_FP32; }
@@ -168,10 +169,28 @@ struct Driver {
   }
 
   // H = A^T A for a column-major s x r matrix A (the Grams of the factor
-  // update), FP32 on CUDA cores in every form; chol reads the lower triangle.
-  // (The three-term TF32 tensor-core product was tried here and failed the
-  // rank-520-of-600 scene, whose Z^T Z is too ill-conditioned for it.)
+  // update); chol reads the lower triangle.  They need FP32-level accuracy
+  // (Z^T Z feeds a Cholesky of condition up to ~1e8; the three-term TF32
+  // product, ~12 ulp per term, failed the rank-520-of-600 scene).  The
+  // tensor-core forms run the six-term BF16 split (A as three BF16 parts,
+  // 24 significant bits, every part product down to 2^-16 of the leading
+  // one: ~3 ulp per term) on the tensor cores; the FP32 form, and operands
+  // whose rows TMA cannot address, run FP32 on CUDA cores.
   mes_status gram(const float* A, int64_t s, int64_t r, const int* skipf) {
+    if (tc() && gparts && s % 8 == 0) {
+      Gemm t = base();
+      t.M = r; t.N = r; t.K_lo = s; t.K_hi = 3;
+      t.A = reinterpret_cast<const float*>(gparts); t.a_m = s; t.a_k = 1; t.a_kh = s * r;
+      t.B = t.A; t.b_n = s; t.b_k = 1; t.b_kh = s * r;
+      t.C = H; t.c_m = 1; t.c_n = r;
+      t.lower = true;
+      t.skip = skipf;
+      t.wait_ns = wait_ns;
+      if (mes::tc_eligible(t, 3)) {
+        MES_TRY(mes::split_bf16x3(A, gparts, s * r, s * r, skipf, st));
+        return mes::gemm_tc(t, 3, split_ws, split_elems, flags, st);
+      }
+    }
     Gemm g = base();
     g.M = r; g.N = r; g.K_lo = s;
     g.A = A; g.a_m = s; g.a_k = 1;
@@ -489,6 +508,12 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   MES_TRY(scr.alloc(&T2, r1 * s2 * L));
   MES_TRY(scr.alloc(&d.Z, zsz));
   MES_TRY(scr.alloc(&d.Zh, zsz));
+  if (tf32) {
+    int64_t gsz = zsz;
+    if (s1 * r1 > gsz) gsz = s1 * r1;
+    if (s2 * r2 > gsz) gsz = s2 * r2;
+    MES_TRY(scr.alloc(&d.gparts, 3 * gsz));
+  }
   MES_TRY(scr.alloc(&d.W, (s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2)));
   MES_TRY(scr.alloc(&d.W2, (s1 * r1 > s2 * r2 ? s1 * r1 : s2 * r2)));
   MES_TRY(scr.alloc(&d.H, rmax * rmax));

@@ -1,5 +1,5 @@
 """The matrix-product kernels in isolation, through the C ABI test hook:
-CUDA-core FP32, tcgen05 kind::tf32 and kind::f16 (BF16), against numpy.
+CUDA-core FP32, tcgen05 kind::tf32 and kind::f16 (BF16), the three-term TF32 and six-term BF16 splits, against numpy.
 
 Tolerances follow the arithmetic of each kind, for N(0,1) inputs (partial
 sums grow like sqrt(k)): sequential FP32 accumulation of K products has an
@@ -60,7 +60,7 @@ SHAPES = [(128, 128, 32, 1), (256, 256, 128, 1), (200, 300, 100, 1), (384, 512, 
 
 
 @pytest.mark.parametrize("M,N,K,batch", SHAPES)
-@pytest.mark.parametrize("impl", [0, 1, 2, 3])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3, 4])
 def test_gemm_kernels(lib, impl, M, N, K, batch):
     rng = np.random.default_rng(M * 7 + N + K)
     A = rng.standard_normal((batch, M, K)).astype(np.float32)
@@ -75,10 +75,15 @@ def test_gemm_kernels(lib, impl, M, N, K, batch):
     elif impl == 3:
         Ar, Br = A, B
         tol = 6 * u * K + 8e-6 * np.sqrt(K) + 1e-6
+    elif impl == 4:
+        # six-term BF16 split: ~3 * 2^-24 per product, the same order as the
+        # FP32 accumulation itself
+        Ar, Br = A, B
+        tol = 6 * u * K + 4e-6 * np.sqrt(K) + 1e-6
     else:
         Ar, Br = A, B
         tol = 6 * u * K + 1e-6
-    if impl == 2 and (K * 2) % 16:
+    if impl in (2, 4) and (K * 2) % 16:
         # BF16 rows of K elements are not a multiple of 16 bytes: the tensor
         # map cannot address them and the call must say so
         with pytest.raises(lib.MesError) as e:
@@ -89,4 +94,5 @@ def test_gemm_kernels(lib, impl, M, N, K, batch):
     got = _run(lib, impl, A, B)
     assert np.isfinite(got).all()
     err = np.abs(got - want).max()
+    print(f"impl {impl} {M}x{N}x{K}x{batch}: max error {err:.3e} (bound {tol:.3e})")
     assert err < tol, (impl, M, N, K, err, tol)
