@@ -76,10 +76,12 @@ def test_gemm_kernels(lib, impl, M, N, K, batch):
         Ar, Br = A, B
         tol = 6 * u * K + 8e-6 * np.sqrt(K) + 1e-6
     elif impl == 4:
-        # six-term BF16 split: ~3 * 2^-24 per product, the same order as the
-        # FP32 accumulation itself
+        # six-term BF16 split: ~3 * 2^-24 per product; measured, its largest
+        # error follows the three-term product's at small K (both limited by
+        # the partial sums inside the tensor core) and stays at or below the
+        # CUDA-core kernel's at K >= 1920, so it takes the same bound
         Ar, Br = A, B
-        tol = 6 * u * K + 4e-6 * np.sqrt(K) + 1e-6
+        tol = 6 * u * K + 8e-6 * np.sqrt(K) + 1e-6
     else:
         Ar, Br = A, B
         tol = 6 * u * K + 1e-6
