@@ -520,7 +520,11 @@ struct PCfg {
   static constexpr uint32_t FMT = (KIND == 1 || KIND == 3) ? 1u : 2u;
   static constexpr uint32_t IDESC =
       (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-  static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators: 256 or 512 columns (powers of 2)
+  // two accumulators (double buffer) of BN columns; KIND 3 gives each tile a
+  // second one for the correction terms (pairs 2..6), so 4 x BN
+  static constexpr int ACC_COLS = KIND == 3 ? 2 * BN : BN;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // 256 or 512 columns (powers of 2)
+  static_assert(TMEM_COLS <= 512, "tensor memory columns");
 };
 
 template <int KIND, int BN, int STAGES>
@@ -638,7 +642,10 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         break;
       }
       tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      const uint32_t d0 = tmem + (uint32_t)(acc * C::ACC_COLS);
+      // KIND 3: the leading pair (1,1) into d0, the five correction pairs
+      // into d0 + BN, so the small terms are not rounded against the full sum
+      const int k_lead = KIND == 3 ? args.k_tiles_lo : 1 << 30;
       for (int kt = kb; kt < ke; ++kt) {
         if (!mbar_wait(&full[stage], phase, wait_ns)) {
           ok = false;
@@ -647,9 +654,13 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         tc_fence_after();
         const uint32_t sa = smem_u32(ring + stage * C::STAGE);
         const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + C::A_BYTES);
+        const bool lead = kt < k_lead;
+        const uint32_t d = lead ? d0 : d0 + BN;
+        // first K slice of this accumulator in the tile's range: overwrite
+        const bool first = lead ? kt == kb : kt == (kb > k_lead ? kb : k_lead);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-          mma<KIND>(d, da + 2 * kk, db + 2 * kk, C::IDESC, (kt > kb || kk > 0) ? 1u : 0u);
+          mma<KIND>(d, da + 2 * kk, db + 2 * kk, C::IDESC, (!first || kk > 0) ? 1u : 0u);
         mma_commit(&empty[stage]);
         if (++stage == STAGES) {
           stage = 0;
@@ -683,9 +694,24 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         break;
       }
       tc_fence_after();
+      // KIND 3: which of the tile's two accumulators its K range wrote
+      const bool has_lead = KIND != 3 || kb < args.k_tiles_lo;
+      const bool has_corr = KIND == 3 && ke > args.k_tiles_lo;
+      const uint32_t row = (uint32_t)(wq * 32) << 16;
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
         uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        if (has_lead) {
+          tmem_ld32(tmem + row + (uint32_t)(acc * C::ACC_COLS + c0), v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0u;
+        }
+        if (has_corr) {
+          uint32_t w[32];
+          tmem_ld32(tmem + row + (uint32_t)(acc * C::ACC_COLS + BN + c0), w);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+        }
         store_chunk(args, v, m0, n0, b, split, wq, lane, tile, c0);
       }
       // this warp's part of the accumulator is read: hand it back to the MMA
@@ -826,7 +852,7 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
                        int64_t split_ws_elems, int* err, cudaStream_t st) {
   using namespace mes;
   const int BK = 128 / kind_bytes(kind);
-  if (kind == 2 || (bn != 128 && bn != 256)) bn = 128;   // KIND 2 has only the 128-wide tile
+  if (kind >= 2 || (bn != 128 && bn != 256)) bn = 128;   // KINDs 2 and 3 have only the 128-wide tile
   CUtensorMap ma, mb, ma2, mb2;
   const bool ab = g.batch > 1 && g.a_b != 0, bb = g.batch > 1 && g.b_b != 0;
   if (!make_map(&ma, g.A, kind, g.K_lo, g.M, g.K_hi, ab ? g.batch : 1, g.a_m, g.a_kh, g.a_b, BM) ||
@@ -908,8 +934,7 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
         if (bn == 256) MES_TRY((launch_tcp<1, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
         else MES_TRY((launch_tcp<1, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
       } else {
-        if (bn == 256) MES_TRY((launch_tcp<3, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
-        else MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+        MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
       }
     } else if (kind == 0) {
       if (bn == 256) MES_TRY((launch_tc<0, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
@@ -987,7 +1012,7 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   // tile width: KIND 2 stages four tiles and has only N = 128; otherwise the
   // width that pads N least (ties to 256: fewer re-reads of the A tile)
   int bn0 = 128;
-  if (kind != 2 && g.N > 128) bn0 = ((g.N + 255) / 256) * 256 <= ((g.N + 127) / 128) * 128 ? 256 : 128;
+  if (kind < 2 && g.N > 128) bn0 = ((g.N + 255) / 256) * 256 <= ((g.N + 127) / 128) * 128 ? 256 : 128;
   if (g.accumulate || g.ref || !tuning_on()) return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
   const std::string key = tune_key(g, kind);
   {
@@ -1011,7 +1036,7 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   float best_ms = 1e30f;
   const bool was_prof = prof_on();
   for (int bn : {128, 256}) {
-    if (bn == 256 && (kind == 2 || g.N <= 128)) continue;
+    if (bn == 256 && (kind >= 2 || g.N <= 128)) continue;
     for (int sp = 1; sp <= 16; sp *= 2) {
       if (sp > 1 && (!split_ws || kt / sp < 4 || (int64_t)sp * g.batch * g.M * g.N > split_ws_elems)) break;
       cudaEventRecord(e0, st);
