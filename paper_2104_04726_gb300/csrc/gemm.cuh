@@ -49,6 +49,12 @@ struct Gemm {
   int64_t split_elems = 0;
   // Bound of each pipeline wait of the tensor-core kernel in ns (0: 2 s).
   uint64_t wait_ns = 0;
+  // Tensor-core kinds 0 and 1 only, C with m contiguous (c_m == 1): also
+  // write the three BF16 parts of every stored value (as split_bf16x3 makes
+  // them) to Cp[part * cp_plane + offset of C], the operand of a six-term
+  // product that follows.
+  uint16_t* Cp = nullptr;
+  int64_t cp_plane = 0;
 };
 
 // FP32 CUDA-core path.

@@ -71,7 +71,18 @@ struct TcArgs {
   int* err;
   uint64_t wait_ns;    // bound of each pipeline wait (0: kWaitNs)
   int lower;           // skip tiles wholly above the diagonal (n0 >= m0 + BM)
+  uint16_t* Cp;        // nullable: BF16 parts of C (c_m == 1), planes of cp_plane
+  int64_t cp_plane;
 };
+
+// The three BF16 parts x1 = bf(x), x2 = bf(x - x1), x3 = bf(x - x1 - x2),
+// each rounded to nearest even (both differences are exact in FP32).
+__device__ __forceinline__ void bf16x3_parts(float x, uint16_t& b1, uint16_t& b2, uint16_t& b3) {
+  b1 = mes::bf16_bits(x);
+  const float r1 = x - __uint_as_float((uint32_t)b1 << 16);
+  b2 = mes::bf16_bits(r1);
+  b3 = mes::bf16_bits(r1 - __uint_as_float((uint32_t)b2 << 16));
+}
 
 // Element bytes of an operand kind: BF16 for kinds 1 and 3, FP32 otherwise.
 __host__ __device__ constexpr int kind_bytes(int kind) { return (kind == 1 || kind == 3) ? 2 : 4; }
@@ -259,6 +270,14 @@ __device__ __forceinline__ void store_chunk(const TcArgs& args, const uint32_t (
       float w = args.accumulate ? *p + val[j] : val[j];
       if (args.round_out) w = mes::round_tf32(w);
       *p = w;
+      if (args.Cp) {   // lanes are consecutive m: each part store is 64 contiguous bytes
+        uint16_t b1, b2, b3;
+        bf16x3_parts(w, b1, b2, b3);
+        uint16_t* q = args.Cp + moff + cw.off;
+        q[0] = b1;
+        q[args.cp_plane] = b2;
+        q[2 * args.cp_plane] = b3;
+      }
     }
   }
   if (args.C2) {
@@ -508,7 +527,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 // on a timeout a role sets its error bit and leaves its loop, and the
 // teardown drains loads and MMAs in flight as in tc_gemm_kernel.
 // --------------------------------------------------------------------------
-template <int KIND, int BN, int STAGES>
+template <int KIND, int BN, int STAGES, int CTAS = 1>
 struct PCfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
@@ -517,6 +536,7 @@ struct PCfg {
   static constexpr int BAR = 8 * (2 * STAGES + 5);
   static constexpr int SMEM = STAGES * STAGE + EPI + 1024 /*align*/ + BAR + 16;
   static_assert(SMEM <= 232448, "shared memory per CTA");
+  static_assert(CTAS * (SMEM + 1024) <= 233472, "shared memory per SM");
   static constexpr uint32_t FMT = (KIND == 1 || KIND == 3) ? 1u : 2u;
   static constexpr uint32_t IDESC =
       (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -524,14 +544,14 @@ struct PCfg {
   // second one for the correction terms (pairs 2..6), so 4 x BN
   static constexpr int ACC_COLS = KIND == 3 ? 2 * BN : BN;
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // 256 or 512 columns (powers of 2)
-  static_assert(TMEM_COLS <= 512, "tensor memory columns");
+  static_assert(CTAS * TMEM_COLS <= 512, "tensor memory columns per SM");
 };
 
-template <int KIND, int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int KIND, int BN, int STAGES, int CTAS>
+__global__ void __launch_bounds__(kThreads, CTAS)
 tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const TcArgs args, int mt, int nt, int ntiles) {
-  using C = PCfg<KIND, BN, STAGES>;
+  using C = PCfg<KIND, BN, STAGES, CTAS>;
   if (args.skip && *args.skip) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -746,6 +766,14 @@ __global__ void split_reduce_kernel(const float* __restrict__ ws, TcArgs a) {
     val = a.accumulate ? *p + val : val;
     if (a.round_out) val = mes::round_tf32(val);
     *p = val;
+    if (a.Cp) {
+      uint16_t b1, b2, b3;
+      bf16x3_parts(val, b1, b2, b3);
+      uint16_t* q = a.Cp + (p - a.C);
+      q[0] = b1;
+      q[a.cp_plane] = b2;
+      q[2 * a.cp_plane] = b3;
+    }
     if (a.C2) a.C2[ml * a.c2_m + mh * a.c2_mh + nl * a.c2_n + nh * a.c2_nh + b * a.c2_b] = val;
   }
 }
@@ -807,18 +835,19 @@ mes_status launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const CUtenso
   return MES_OK;
 }
 
-template <int KIND, int BN, int STAGES>
+template <int KIND, int BN, int STAGES, int CTAS = 1>
 mes_status launch_tcp(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, int mt, int nt, int ntiles,
                       cudaStream_t st) {
-  using C = PCfg<KIND, BN, STAGES>;
+  using C = PCfg<KIND, BN, STAGES, CTAS>;
   static bool attr = false;
   if (!attr) {
-    MES_CUDA_TRY(cudaFuncSetAttribute(tcp_gemm_kernel<KIND, BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      C::SMEM));
+    MES_CUDA_TRY(cudaFuncSetAttribute(tcp_gemm_kernel<KIND, BN, STAGES, CTAS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     attr = true;
   }
-  const int grid = ntiles < mes::sm_count() ? ntiles : mes::sm_count();
-  tcp_gemm_kernel<KIND, BN, STAGES><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a, mt, nt, ntiles);
+  const int slots = CTAS * mes::sm_count();
+  const int grid = ntiles < slots ? ntiles : slots;
+  tcp_gemm_kernel<KIND, BN, STAGES, CTAS><<<grid, kThreads, C::SMEM, st>>>(ma, mb, a, mt, nt, ntiles);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
@@ -874,6 +903,10 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   // part pairs
   a.k_tiles_total = a.k_tiles_lo * (kind == 3 ? 6 : (int)g.K_hi);
   a.lower = g.lower ? 1 : 0;
+  a.Cp = g.Cp;
+  a.cp_plane = g.cp_plane;
+  if (g.Cp && (kind >= 2 || g.c_m != 1 || g.ref))
+    return fail(MES_ERR_INVALID_ARG, "gemm_tc: BF16 parts need kind 0 or 1 and an m-contiguous C");
   a.batch = g.batch;
   a.a_batched = ab ? 1 : 0;
   a.b_batched = bb ? 1 : 0;
@@ -922,19 +955,26 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
     const bool rs = g.ref != nullptr;
     const int mt = (int)((g.M + BM - 1) / BM), nt = (int)((g.N + bn - 1) / bn);
     const int64_t ntiles = (int64_t)mt * nt * g.batch * splits;
-    static const bool classic = getenv("MES_TC_CLASSIC") != nullptr;
+    // MES_TC_VARIANT (measurement switch for the products of kinds 0 and 1):
+    // unset = one tile per CTA; "p1" = persistent, one CTA per SM; "p2" =
+    // persistent, 128-wide tiles, two CTAs per SM
+    static const char* variant = getenv("MES_TC_VARIANT");
+    const int pv = (variant && variant[0] == 'p') ? (variant[1] == '2' ? 2 : 1) : 0;
     if (kind == 3 && (rs || g.accumulate || ntiles >= INT32_MAX))
       return fail(MES_ERR_INVALID_ARG, "gemm_tc: the six-term product has no residual or accumulate mode");
-    if (kind == 3 || (kind != 2 && !rs && !g.accumulate && !classic && ntiles < INT32_MAX)) {
+    if (kind == 3) {
+      MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+    } else if (pv && kind != 2 && !rs && !g.accumulate && ntiles < INT32_MAX && (pv == 1 || bn == 128)) {
       // persistent kernel: tiles looped per CTA, double-buffered accumulator
-      if (kind == 0) {
+      if (pv == 2) {
+        if (kind == 0) MES_TRY((launch_tcp<0, 128, 2, 2>(ma, mb, a, mt, nt, (int)ntiles, st)));
+        else MES_TRY((launch_tcp<1, 128, 2, 2>(ma, mb, a, mt, nt, (int)ntiles, st)));
+      } else if (kind == 0) {
         if (bn == 256) MES_TRY((launch_tcp<0, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
         else MES_TRY((launch_tcp<0, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
-      } else if (kind == 1) {
+      } else {
         if (bn == 256) MES_TRY((launch_tcp<1, 256, 4>(ma, mb, a, mt, nt, (int)ntiles, st)));
         else MES_TRY((launch_tcp<1, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
-      } else {
-        MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
       }
     } else if (kind == 0) {
       if (bn == 256) MES_TRY((launch_tc<0, 256, 2>(ma, mb, ma2, mb2, a, grid, rs, st)));
@@ -1012,7 +1052,9 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   // tile width: KIND 2 stages four tiles and has only N = 128; otherwise the
   // width that pads N least (ties to 256: fewer re-reads of the A tile)
   int bn0 = 128;
-  if (kind < 2 && g.N > 128) bn0 = ((g.N + 255) / 256) * 256 <= ((g.N + 127) / 128) * 128 ? 256 : 128;
+  static const char* variant = getenv("MES_TC_VARIANT");
+  const bool p2 = variant && variant[0] == 'p' && variant[1] == '2';
+  if (kind < 2 && g.N > 128 && !p2) bn0 = ((g.N + 255) / 256) * 256 <= ((g.N + 127) / 128) * 128 ? 256 : 128;
   if (g.accumulate || g.ref || !tuning_on()) return gemm_tc_cfg(g, kind, bn0, 0, split_ws, split_ws_elems, err, st);
   const std::string key = tune_key(g, kind);
   {
@@ -1094,14 +1136,11 @@ __global__ void split_bf16x3_kernel(const float* __restrict__ in, uint16_t* __re
                                     int64_t plane, const int* __restrict__ skip) {
   if (skip && *skip) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float x = in[i];
-    const uint16_t b1 = mes::bf16_bits(x);
-    const float r1 = x - __uint_as_float((uint32_t)b1 << 16);
-    const uint16_t b2 = mes::bf16_bits(r1);
-    const float r2 = r1 - __uint_as_float((uint32_t)b2 << 16);
+    uint16_t b1, b2, b3;
+    bf16x3_parts(in[i], b1, b2, b3);
     out[i] = b1;
     out[plane + i] = b2;
-    out[2 * plane + i] = mes::bf16_bits(r2);
+    out[2 * plane + i] = b3;
   }
 }
 

@@ -176,8 +176,15 @@ struct Driver {
   // 24 significant bits, every part product down to 2^-16 of the leading
   // one: ~3 ulp per term) on the tensor cores; the FP32 form, and operands
   // whose rows TMA cannot address, run FP32 on CUDA cores.
-  mes_status gram(const float* A, int64_t s, int64_t r, const int* skipf) {
-    if (tc() && gparts && s % 8 == 0) {
+  // True when gram(A, s, r) runs on the tensor cores, so the product that
+  // makes A can write its BF16 parts to gparts (Gemm::Cp) instead of a split
+  // pass over A.
+  bool gram_tc(int64_t s) const { return tc() && gparts && s % 8 == 0; }
+
+  // parts_ready: A's three BF16 parts are already in gparts (written by the
+  // product that made A)
+  mes_status gram(const float* A, int64_t s, int64_t r, const int* skipf, bool parts_ready = false) {
+    if (gram_tc(s)) {
       Gemm t = base();
       t.M = r; t.N = r; t.K_lo = s; t.K_hi = 3;
       t.A = reinterpret_cast<const float*>(gparts); t.a_m = s; t.a_k = 1; t.a_kh = s * r;
@@ -187,9 +194,10 @@ struct Driver {
       t.skip = skipf;
       t.wait_ns = wait_ns;
       if (mes::tc_eligible(t, 3)) {
-        MES_TRY(mes::split_bf16x3(A, gparts, s * r, s * r, skipf, st));
+        if (!parts_ready) MES_TRY(mes::split_bf16x3(A, gparts, s * r, s * r, skipf, st));
         return mes::gemm_tc(t, 3, split_ws, split_elems, flags, st);
       }
+      if (parts_ready) return mes::fail(MES_ERR_INVALID_ARG, "gram: parts written for an ineligible Gram");
     }
     Gemm g = base();
     g.M = r; g.N = r; g.K_lo = s;
@@ -203,8 +211,8 @@ struct Driver {
   // One CholeskyQR pass dst = src R^-1 with R^T R = src^T src (equilibrated,
   // starting shift `shift`); every kernel is a no-op when *skipf != 0.
   mes_status cholqr_pass(const float* src, int64_t s, int64_t r, float shift, float* dst, const int* skipf,
-                         int* clean) {
-    MES_TRY(gram(src, s, r, skipf));
+                         int* clean, bool parts_ready = false) {
+    MES_TRY(gram(src, s, r, skipf, parts_ready));
     MES_TRY(mes::chol(H, (int)r, shift, cwA, dinv, linv, flags, skipf, st, clean));
     return mes::trsm(src, s, (int)r, cwA, dinv, linv, dst, false, skipf, st);
   }
@@ -218,17 +226,18 @@ struct Driver {
   //          Inside the sweeps W arrives preconditioned by Z^T Z (subspace
   //          step below) with an equilibrated condition number of a few
   //          units, where one pass is orthonormal to FP32 precision.
-  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout, float* Srnd, bool robust) {
+  // parts_ready: Win's BF16 parts are in gparts (see gram)
+  mes_status orth(float* Win, int64_t s, int64_t r, float* Sout, float* Srnd, bool robust, bool parts_ready = false) {
     if (robust) {
       float* src = Win;
       float* bufs[2] = {W2, Win};
       for (int pass = 0; pass < 3; ++pass) {
         float* dst = (pass == 2) ? Sout : bufs[pass & 1];
-        MES_TRY(cholqr_pass(src, s, r, pass == 0 ? kShiftW : 0.f, dst, skip, nullptr));
+        MES_TRY(cholqr_pass(src, s, r, pass == 0 ? kShiftW : 0.f, dst, skip, nullptr, pass == 0 && parts_ready));
         src = dst;
       }
     } else {
-      MES_TRY(cholqr_pass(Win, s, r, 0.f, Sout, skip, clean));
+      MES_TRY(cholqr_pass(Win, s, r, 0.f, Sout, skip, clean, parts_ready));
       MES_TRY(cholqr_pass(Sout, s, r, 0.f, Win, clean, nullptr));   // only if pass 1 restarted
       MES_TRY(mes::copy_if(Win, Sout, s * r, clean, st));
     }
@@ -248,23 +257,31 @@ struct Driver {
     Gemm gz = z16 ? *z16 : zdesc;
     gz.B = z16 ? reinterpret_cast<const float*>(S16) : (tc() ? Srnd : S); gz.b_n = s; gz.b_k = 1;
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
+    // the Gram's BF16 parts straight from the product's epilogue
+    const bool zparts = gram_tc(J) && (z16 || mes::tc_eligible(gz, 0));
+    if (zparts) { gz.Cp = gparts; gz.cp_plane = J * r; }
     MES_TRY(z16 ? big16(gz) : big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
-    MES_TRY(gram(Z, J, r, skip));
+    MES_TRY(gram(Z, J, r, skip, zparts));
     MES_TRY(mes::chol(H, (int)r, kShiftZ, cwA, dinv, linv, flags, skip, st));
     // Zh = Z R_z^-1, an operand of the next product: TF32-rounded in those forms
     MES_TRY(mes::trsm(Z, J, (int)r, cwA, dinv, linv, Zh, tc(), skip, st));
     // W = Y Zh   (s x r)
     Gemm gw = w16 ? *w16 : wdesc;
     gw.C = W; gw.c_m = 1; gw.c_n = s;
+    bool wparts = false;
     if (w16) {
       MES_TRY(mes::to_bf16(Zh, Zh16, J * r, skip, st));
       gw.B = reinterpret_cast<const float*>(Zh16);
+      wparts = gram_tc(s);
+      if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big16(gw));
     } else {
+      wparts = gram_tc(s) && mes::tc_eligible(gw, 0);
+      if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big(gw));
     }
-    MES_TRY(orth(W, s, r, S, Srnd, robust));
+    MES_TRY(orth(W, s, r, S, Srnd, robust, wparts));
     if (S16) MES_TRY(mes::to_bf16(S, S16, s * r, skip, st));
     return MES_OK;
   }
