@@ -564,6 +564,8 @@ def main():
                     help="Poisson arrival rate of the serving form (capped at 80%% of the measured capacity)")
     ap.add_argument("--batch-stacks", type=int, default=64,
                     help="stacks of the batched-form measurement (0 = skip it)")
+    ap.add_argument("--no-concurrency-hint", dest="concurrency_hint", action="store_false",
+                    help="run every decomposition as if alone (split-K fills all SMs)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -634,8 +636,11 @@ def main():
                     self.rgb.copy_(self.rgb_host, non_blocking=True)
                 mes.colour_convert(self.rgb, cfg["space"], out=self.X, norm2=self.n2)
                 # the fit's reconstruction pass (fused residual) also stores T_hat
+                # S decompositions run side by side: each splits its products'
+                # reductions over its share of the SMs (the concurrency hint)
                 mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=precision,
-                               outputs=(self.core, self.facs, self.fit, self.itd, None), reconstruction=self.Xh)
+                               outputs=(self.core, self.facs, self.fit, self.itd, None), reconstruction=self.Xh,
+                               concurrency=S if args.concurrency_hint else 0)
                 q, sc = mes.quantize_core(self.core, ranks, 16)
                 if e2e:
                     self.q_host.copy_(q, non_blocking=True)

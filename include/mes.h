@@ -180,6 +180,17 @@ typedef struct mes_als_opts {
                            2 s).  A wait that runs out sets the timeout status
                            and the kernel finishes without hanging; a bound of
                            a few ns forces that path (tests of error handling) */
+  int concurrency;      /* how many decompositions the caller keeps running
+                           side by side on this GPU (0 or 1: this one alone).
+                           Products whose tile grid does not fill the GPU
+                           split their reduction dimension over at most
+                           SMs / concurrency CTA slots instead of all SMs:
+                           less SM time (fewer partial sums to write and
+                           reduce), a longer single call.  Results do not
+                           depend on it beyond rounding order (bitwise
+                           reproducible for a given value).  The batched and
+                           served forms set it from their stream / slot count
+                           when a problem leaves it 0.                        */
 } mes_als_opts;
 
 /*

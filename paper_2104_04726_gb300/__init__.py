@@ -117,7 +117,7 @@ def colour_invert(X, space: str = "ycbcr", gamma: float = 2.2, rgb8=None, rgbp=N
 def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20, tol: float = 0.0,
                precision: str = "fp32", init_iters: int = 0, inner_iters: int = 0, seed: int = 0,
                canonical: bool = True, init_factors=None, history: bool = False, outputs=None,
-               init: str = "thosvd", reconstruction=None, wait_ns: int = 0):
+               init: str = "thosvd", reconstruction=None, wait_ns: int = 0, concurrency: int = 0):
     """Tucker-ALS / HOOI (Section III-B).  X: float32 CUDA tensor holding the
     first-mode-fastest tensor of paper dims `dims`.  Returns a dict with
     `core` (torch shape reversed(ranks)), `factors` (list of (r_n, s_n)
@@ -128,7 +128,8 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     CUDA tensor like X that receives T_hat (Eq. 1) from the fit's pass.
     `status` (int32 CUDA scalar) receives the device-side status (0, or
     MES_ERR_TIMEOUT / MES_ERR_NONFINITE, with a NaN fit); wait_ns bounds the
-    tensor-core pipeline waits (0: the library default)."""
+    tensor-core pipeline waits (0: the library default); concurrency: how
+    many decompositions run side by side (split-K over a share of the SMs)."""
     torch = _torch()
     _need(X, torch.float32, "X")
     dims = [int(d) for d in dims]
@@ -168,6 +169,7 @@ def tucker_als(X, dims: Sequence[int], ranks: Sequence[int], max_iters: int = 20
     opts.fit_history = hist.data_ptr() if hist is not None else None
     opts.status = status.data_ptr()
     opts.wait_ns = int(wait_ns)
+    opts.concurrency = int(concurrency)
     keep = None
     if init_factors is not None:
         keep = (ctypes.c_void_p * N)(*[f.data_ptr() for f in init_factors])
@@ -300,7 +302,7 @@ class Problem:
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], X=None, rgb8=None, space: str = "ipt",
                  gamma: float = 2.2, max_iters: int = 20, tol: float = 0.0, precision: str = "fp32",
-                 quant_bits: int = 0, device=None, wait_ns: int = 0):
+                 quant_bits: int = 0, device=None, wait_ns: int = 0, concurrency: int = 0):
         torch = _torch()
         dims = [int(d) for d in dims]
         ranks = [int(r) for r in ranks]
@@ -344,6 +346,7 @@ class Problem:
         p.opts.iters_done = self.iters.data_ptr()
         p.opts.status = self.status.data_ptr()
         p.opts.wait_ns = int(wait_ns)
+        p.opts.concurrency = int(concurrency)   # 0: the batch's streams / the server's slots
         p.core = _ptr(self.core)
         p.fit = _ptr(self.fit)
         p.quant_bits = int(quant_bits)

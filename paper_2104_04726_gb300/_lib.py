@@ -75,6 +75,7 @@ class MesAlsOpts(ctypes.Structure):
         ("reconstruction", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
         ("wait_ns", ctypes.c_int64),
+        ("concurrency", ctypes.c_int),
     ]
 
 

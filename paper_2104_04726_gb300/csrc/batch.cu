@@ -123,7 +123,9 @@ mes_status batch_enqueue(mes_batch* b, const mes_problem* probs, int n, mes_stat
   for (int i : order) {
     const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     load[k] += cost[i];
-    mes_status s = problem_enqueue(probs[i], b->streams[k]);
+    mes_problem pi = probs[i];
+    if (pi.opts.concurrency == 0) pi.opts.concurrency = ns;   // the streams running side by side
+    mes_status s = problem_enqueue(pi, b->streams[k]);
     if (statuses) statuses[i] = s;
     if (s != MES_OK) {
       err = s;
@@ -355,6 +357,7 @@ void serve_loop(mes_server* s) {
       s->peak = std::max(s->peak, s->in_use);
       r.slot = k;
       mes_problem prob = r.p;
+      if (prob.opts.concurrency == 0) prob.opts.concurrency = (int)s->slots.size();
       int* dstat = prob.opts.status ? prob.opts.status : s->dev_status + k;
       prob.opts.status = dstat;
       s->host_status[k] = MES_OK;

@@ -55,6 +55,10 @@ struct Gemm {
   // product that follows.
   uint16_t* Cp = nullptr;
   int64_t cp_plane = 0;
+  // CTA slots the split-K rule fills (0: the SM count).  A caller that runs
+  // several decompositions side by side gives each a share, trading the
+  // latency of one product for less SM time (partials, reduction pass).
+  int64_t fill = 0;
 };
 
 // FP32 CUDA-core path.

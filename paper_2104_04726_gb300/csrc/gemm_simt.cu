@@ -247,7 +247,7 @@ mes_status launch(const mes::Gemm& g, dim3 grid, cudaStream_t st) {
     for (int64_t i = 0; i < (int64_t)grid.x; ++i) lt += std::min<int64_t>(i + 1, grid.y);
     tiles = lt * grid.z;
   }
-  const int64_t sms = mes::sm_count();
+  const int64_t sms = g.fill > 0 ? g.fill : mes::sm_count();
   int splits = 1;
   if (!g.ref && g.split_ws && tiles < sms) {
     // one wave of CTAs (the register tile allows one per SM), at least 8

@@ -929,11 +929,12 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   const int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + bn - 1) / bn) * g.batch;
   int splits = 1;
   const int64_t sms = sm_count();
+  const int64_t fill = g.fill > 0 ? g.fill : sms;   // CTA slots the split rule aims at
   if (want_splits > 0 && !g.ref &&
       (want_splits == 1 || (split_ws && (int64_t)want_splits * g.batch * g.M * g.N <= split_ws_elems))) {
     splits = want_splits;   // a tuned factor the workspace can hold
   } else if (!g.ref && split_ws) {
-    while (tiles * splits * 2 <= sms && a.k_tiles_total / (splits * 2) >= 4 &&
+    while (tiles * splits * 2 <= fill && a.k_tiles_total / (splits * 2) >= 4 &&
            (int64_t)(splits * 2) * g.batch * g.M * g.N <= split_ws_elems)
       splits *= 2;
   }

@@ -120,6 +120,7 @@ struct Driver {
 
   int prec = MES_PREC_FP32;
   uint64_t wait_ns = 0;                     // bound of the tensor-core pipeline waits (0: default)
+  int64_t fill = 0;                         // CTA slots for split-K (0: all SMs)
   float* split_ws = nullptr;
   int64_t split_elems = 0;
   uint16_t* Zh16 = nullptr;                 // BF16 copy of Zh (BF16 form, T-side steps)
@@ -132,6 +133,7 @@ struct Driver {
   mes_status gemm(const Gemm& g) {
     Gemm h = g;
     h.skip = skip;
+    h.fill = fill;
     h.split_ws = split_ws;
     h.split_elems = split_elems;
     return mes::gemm_f32(h, st);
@@ -143,6 +145,7 @@ struct Driver {
     Gemm h = g;
     h.skip = skip;
     h.wait_ns = wait_ns;
+    h.fill = fill;
     if (tc() && mes::tc_eligible(h, 0))
       return mes::gemm_tc(h, 0, split_ws, split_elems, flags, st);
     h.split_ws = split_ws;
@@ -156,6 +159,7 @@ struct Driver {
     Gemm h = g;
     h.skip = skip;
     h.wait_ns = wait_ns;
+    h.fill = fill;
     return mes::gemm_tc(h, 1, split_ws, split_elems, flags, st);
   }
 
@@ -163,6 +167,7 @@ struct Driver {
   mes_status gemm_if(const Gemm& g, const int* skipf) {
     Gemm h = g;
     h.skip = skipf;
+    h.fill = fill;
     h.split_ws = split_ws;
     h.split_elems = split_elems;
     return mes::gemm_f32(h, st);
@@ -180,6 +185,7 @@ struct Driver {
   // makes A can write its BF16 parts to gparts (Gemm::Cp) instead of a split
   // pass over A.
   bool gram_tc(int64_t s) const { return tc() && gparts && s % 8 == 0; }
+  bool fuse_parts = getenv("MES_NO_FUSED_PARTS") == nullptr;
 
   // parts_ready: A's three BF16 parts are already in gparts (written by the
   // product that made A)
@@ -193,6 +199,7 @@ struct Driver {
       t.lower = true;
       t.skip = skipf;
       t.wait_ns = wait_ns;
+      t.fill = fill;
       if (mes::tc_eligible(t, 3)) {
         if (!parts_ready) MES_TRY(mes::split_bf16x3(A, gparts, s * r, s * r, skipf, st));
         return mes::gemm_tc(t, 3, split_ws, split_elems, flags, st);
@@ -258,7 +265,7 @@ struct Driver {
     gz.B = z16 ? reinterpret_cast<const float*>(S16) : (tc() ? Srnd : S); gz.b_n = s; gz.b_k = 1;
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
     // the Gram's BF16 parts straight from the product's epilogue
-    const bool zparts = gram_tc(J) && (z16 || mes::tc_eligible(gz, 0));
+    const bool zparts = fuse_parts && gram_tc(J) && (z16 || mes::tc_eligible(gz, 0));
     if (zparts) { gz.Cp = gparts; gz.cp_plane = J * r; }
     MES_TRY(z16 ? big16(gz) : big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
@@ -273,11 +280,11 @@ struct Driver {
     if (w16) {
       MES_TRY(mes::to_bf16(Zh, Zh16, J * r, skip, st));
       gw.B = reinterpret_cast<const float*>(Zh16);
-      wparts = gram_tc(s);
+      wparts = fuse_parts && gram_tc(s);
       if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big16(gw));
     } else {
-      wparts = gram_tc(s) && mes::tc_eligible(gw, 0);
+      wparts = fuse_parts && gram_tc(s) && mes::tc_eligible(gw, 0);
       if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big(gw));
     }
@@ -448,6 +455,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (o.init != MES_INIT_THOSVD && o.init != MES_INIT_INTERLACED)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: unknown init %d", o.init);
   if (o.wait_ns < 0) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: wait_ns must be >= 0");
+  if (o.concurrency < 0) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: concurrency must be >= 0");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mes::AuditScope audit_scope;
@@ -466,6 +474,11 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   d.st = st;
   d.scr = &scr;
   d.wait_ns = (uint64_t)o.wait_ns;
+  if (o.concurrency > 1) {
+    // each decomposition's share of the SMs (at least 4 CTA slots)
+    const int64_t share = mes::sm_count() / o.concurrency;
+    d.fill = share > 4 ? share : 4;
+  }
 
   const int64_t s1 = sh.s1, s2 = sh.s2, r1 = sh.r1, r2 = sh.r2, L = sh.L, Lr = sh.Lr;
   const int64_t rmax = r1 > r2 ? r1 : r2;
