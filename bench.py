@@ -218,8 +218,8 @@ def run_reference(args):
             "config": conf,
             "sample_per_step": samples[-1]["sample"],
             "extrapolated_from_sweeps": 1,
-            "value_note": ("each step times one sample (one sweep of the 20); value = stacks_per_step / "
-                           "seconds per step, i.e. the sample's sweep time scaled to 20 sweeps"),
+            "value_note": (f"each step times one sample (one sweep of the {cfg['iters']}); value = stacks_per_step "
+                           f"/ seconds per step, i.e. the sample's sweep time scaled to {cfg['iters']} sweeps"),
             "cpu_baseline": {"value": val, "unit": "stacks/s", "cores": samples[-1]["cores"], "kind": "oracle",
                              "sample": samples[-1]["sample"]},
             "thread_scaling": oracle_thread_scaling(),
@@ -564,8 +564,9 @@ def main():
                     help="Poisson arrival rate of the serving form (capped at 80%% of the measured capacity)")
     ap.add_argument("--batch-stacks", type=int, default=64,
                     help="stacks of the batched-form measurement (0 = skip it)")
-    ap.add_argument("--no-concurrency-hint", dest="concurrency_hint", action="store_false",
-                    help="run every decomposition as if alone (split-K fills all SMs)")
+    ap.add_argument("--concurrency", type=int, default=None,
+                    help="concurrency hint of every decomposition (default: --stacks, the stacks run side by "
+                         "side; 1: each as if alone, split-K fills all SMs)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -604,6 +605,7 @@ def main():
     ranks = list(cfg["ranks"])
     iters = cfg["iters"]
     S = args.stacks
+    conc = S if args.concurrency is None else args.concurrency
     P = 1
     for r in ranks[2:]:
         P *= r
@@ -640,7 +642,7 @@ def main():
                 # reductions over its share of the SMs (the concurrency hint)
                 mes.tucker_als(self.X, dims, ranks, max_iters=iters, tol=0.0, precision=precision,
                                outputs=(self.core, self.facs, self.fit, self.itd, None), reconstruction=self.Xh,
-                               concurrency=S if args.concurrency_hint else 0)
+                               concurrency=conc)
                 q, sc = mes.quantize_core(self.core, ranks, 16)
                 if e2e:
                     self.q_host.copy_(q, non_blocking=True)
@@ -761,7 +763,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
                 "data": "synthetic",
-                "config": dict(_config(name, cfg, dims, ranks, args.precision, S, world),
+                "config": dict(_config(name, cfg, dims, ranks, args.precision, S, world), concurrency_hint=conc,
                                launch="value: the step captured once as a CUDA graph and replayed; "
                                       "e2e: eager API calls"),
                 "roofline": roof, "rooflines": _family_rooflines(res["fams"], peaks, peak_src, sms),
