@@ -1075,6 +1075,37 @@ eig_mid_kernel(const float* __restrict__ Hin, int r, float* __restrict__ Z, cons
   }
 }
 
+// --------------------------------------------------------------------------
+// rr_update: one refinement step of approximate eigenvectors X of a symmetric
+// r x r matrix A (Rayleigh-Ritz of a large factor, r > 128).  Given
+// G = X^T X and S = X^T A X it writes E with X(I + E) the refined vectors.
+// E follows from the first-order conditions that X(I + E) be orthonormal,
+// E + E^T = I - G, and diagonalise A, S + E^T S + S E = diag (the iterative
+// refinement of Ogita and Aishima, 2018): d_i = S_ii / G_ii,
+//   e_ii = (1 - G_ii) / 2,
+//   e_ij = (S_ij - d_j G_ij) / (d_j - d_i)   (i != j),
+// and where that first-order rotation would not be small (|e_ij| >= 1/2: the
+// two values are too close for the current accuracy of X, including the
+// near-degenerate pairs an FP32 A cannot separate) only the orthonormality
+// part, e_ij = -G_ij / 2, so such a pair stays unrotated.
+// --------------------------------------------------------------------------
+__global__ void rr_update_kernel(const float* __restrict__ S, const float* __restrict__ G, int r,
+                                 float* __restrict__ E) {
+  const int64_t n = (int64_t)r * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % r), j = (int)(e / r);   // column-major: E[i + r j]
+    const float gij = G[e];
+    if (i == j) {
+      E[e] = 0.5f * (1.f - gij);
+      continue;
+    }
+    const float di = S[i + (int64_t)r * i] / G[i + (int64_t)r * i];
+    const float dj = S[j + (int64_t)r * j] / G[j + (int64_t)r * j];
+    const float num = S[e] - dj * gij, den = dj - di;
+    E[e] = (fabsf(num) < 0.5f * fabsf(den)) ? num / den : -0.5f * gij;
+  }
+}
+
 }  // namespace
 
 namespace mes {
@@ -1379,6 +1410,17 @@ mes_status eig_small(const double* G, int n, int r, float* U, double* evals, con
   MES_TRY(audit(U, (size_t)n * r * 4 - 1, "eig_small U"));
   ProfScope prof("eig_small_f64", st, 0.0, 8.0 * n * n);
   eig_small_kernel<<<1, 32, 0, st>>>(G, n, r, U, evals, skip);
+  MES_LAUNCH_CHECK();
+  return MES_OK;
+}
+
+mes_status rr_update(const float* S, const float* G, int r, float* E, cudaStream_t st) {
+  const size_t last = (size_t)r * r * 4 - 1;
+  MES_TRY(audit(S, last, "rr_update S"));
+  MES_TRY(audit(G, last, "rr_update G"));
+  MES_TRY(audit(E, last, "rr_update E"));
+  ProfScope prof("rr_update", st, 0.0, 12.0 * r * (double)r);
+  rr_update_kernel<<<grid_for((int64_t)r * r, 256, (int64_t)sm_count() * 4), 256, 0, st>>>(S, G, r, E);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }

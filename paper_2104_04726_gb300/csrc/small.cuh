@@ -84,6 +84,10 @@ mes_status trsm(const float* W, int64_t s, int r, const float* L, const float* d
 mes_status eig_small(const double* G, int n, int r, float* U, double* evals, const int* skip,
                      cudaStream_t st);
 mes_status eig_mid(const float* H, int r, float* Z, const int* skip, cudaStream_t st);
+// One refinement step of approximate eigenvectors X of a symmetric A from
+// G = X^T X and S = X^T A X: E with X (I + E) the refined vectors (r x r,
+// column-major).
+mes_status rr_update(const float* S, const float* G, int r, float* E, cudaStream_t st);
 
 // colour.cu / quant.cu
 mes_status colour_launch(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K, int space,

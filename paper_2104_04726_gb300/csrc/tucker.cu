@@ -51,6 +51,8 @@ using mes::KronDesc;
 // first CholeskyQR pass (the Cholesky kernel raises them on breakdown).
 constexpr float kShiftZ = 1e-5f;
 constexpr float kShiftW = 1e-5f;
+// Refinement steps of the Rayleigh-Ritz rotation for ranks above 128.
+constexpr int kRRSteps = 4;
 
 struct Shape {
   int N = 0;
@@ -566,6 +568,8 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   d.clean = done + 4;
   MES_TRY(scr.alloc(&sign, rmax));
   MES_TRY(scr.alloc(&order, rmax));
+  float* rrw = nullptr;   // Rayleigh-Ritz refinement workspace (r > 128): G, HX, S, E, X'
+  if (canonical && rmax > 128) MES_TRY(scr.alloc(&rrw, 5 * rmax * rmax));
   d.flags = flags;
   if (ws_bytes) {
     // the fit's reconstruction with fused residual draws from the same
@@ -911,10 +915,54 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       MES_TRY(d.gemm(gh));
       const int64_t stride = n == 0 ? 1 : r1;
       if (r <= 128) {
-        // Z = eigenvectors of H (FP32 Jacobi), then one CholeskyQR pass on Z
-        // so the rotation is orthogonal to FP32 precision: the accumulated
-        // Jacobi rotations drift by ~sqrt(#rotations) ulp.
+        // Z = eigenvectors of H (FP32 Jacobi, sorted by decreasing eigenvalue)
         MES_TRY(mes::eig_mid(d.H, (int)r, d.cwX, nullptr, st));
+      } else {
+        // Rayleigh-Ritz for r > 128 by refinement: the sweeps' orthogonal
+        // iteration (every factor update orthonormalises with triangular
+        // factors, so the leading columns converge to the leading
+        // eigenvectors) leaves H nearly diagonal, and X <- X (I + E) with E
+        // from rr_update converges from X = I (quadratically once the
+        // rotations are small); pairs closer than the current accuracy stay
+        // unrotated.  Four steps of four r x r products each.
+        float *Gm = rrw, *HX = rrw + r * r, *Sm = rrw + 2 * r * r, *E = rrw + 3 * r * r, *Xn = rrw + 4 * r * r;
+        float* Xc = d.cwX;
+        MES_TRY(mes::identity_fill(Xc, r, (int)r, st));
+        for (int it = 0; it < kRRSteps; ++it) {
+          Gemm gg = base();   // Gm = X^T X
+          gg.M = r; gg.N = r; gg.K_lo = r;
+          gg.A = Xc; gg.a_m = r; gg.a_k = 1;
+          gg.B = Xc; gg.b_n = r; gg.b_k = 1;
+          gg.C = Gm; gg.c_m = 1; gg.c_n = r;
+          MES_TRY(d.gemm(gg));
+          Gemm ga = base();   // HX = H X
+          ga.M = r; ga.N = r; ga.K_lo = r;
+          ga.A = d.H; ga.a_m = 1; ga.a_k = r;
+          ga.B = Xc; ga.b_n = r; ga.b_k = 1;
+          ga.C = HX; ga.c_m = 1; ga.c_n = r;
+          MES_TRY(d.gemm(ga));
+          Gemm gs = base();   // Sm = X^T H X
+          gs.M = r; gs.N = r; gs.K_lo = r;
+          gs.A = Xc; gs.a_m = r; gs.a_k = 1;
+          gs.B = HX; gs.b_n = r; gs.b_k = 1;
+          gs.C = Sm; gs.c_m = 1; gs.c_n = r;
+          MES_TRY(d.gemm(gs));
+          MES_TRY(mes::rr_update(Sm, Gm, (int)r, E, st));
+          MES_CUDA_TRY(cudaMemcpyAsync(Xn, Xc, sizeof(float) * r * r, cudaMemcpyDeviceToDevice, st));
+          Gemm ge = base();   // Xn = X + X E, then X = Xn
+          ge.M = r; ge.N = r; ge.K_lo = r;
+          ge.A = Xc; ge.a_m = 1; ge.a_k = r;
+          ge.B = E; ge.b_n = r; ge.b_k = 1;
+          ge.C = Xn; ge.c_m = 1; ge.c_n = r;
+          ge.accumulate = true;
+          MES_TRY(d.gemm(ge));
+          MES_CUDA_TRY(cudaMemcpyAsync(Xc, Xn, sizeof(float) * r * r, cudaMemcpyDeviceToDevice, st));
+        }
+      }
+      {
+        // one CholeskyQR pass on Z so the rotation is orthogonal to FP32
+        // precision (accumulated Jacobi rotations drift by ~sqrt(#rotations)
+        // ulp; the refinement is orthonormal to first order only)
         Gemm gzz = base();
         gzz.M = r; gzz.N = r; gzz.K_lo = r;
         gzz.A = d.cwX; gzz.a_m = r; gzz.a_k = 1;
@@ -931,7 +979,11 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
         MES_TRY(d.gemm(gu));
         MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));
         MES_TRY(core_apply(n, d.Rinv));   // Q <- Q x_n Z^T
-      } else {
+      }
+      if (r > 128) {
+        // the refinement does not sort: order by the rotated core's mode-n
+        // Gram diagonal (the Ritz values), decreasing
+        MES_TRY(d.gemm(gh));
         MES_TRY(mes::diag_order(d.H, (int)r, order, st));
         MES_TRY(mes::permute_cols(S, s, (int)r, order, nullptr, d.W, st));
         MES_CUDA_TRY(cudaMemcpyAsync(S, d.W, sizeof(float) * s * r, cudaMemcpyDeviceToDevice, st));

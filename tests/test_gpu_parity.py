@@ -419,6 +419,20 @@ def test_xga_scene_parity(mes):
         k, sin_k = contained_sin(T, ref.factors, n, Us[n])
         print(f"xga mode {n}: leading {k} directions with gap > {GAP_GATE}, sin {sin_k:.2e}")
         assert k >= 4 and sin_k < 1e-3, (n, k, sin_k)
+    # the columns themselves (Rayleigh-Ritz of the r > 128 factors, Section
+    # III-B after Eq. 8: the factor is the Gram's leading eigenvectors): a
+    # column whose eigenvalue is separated from both neighbours by more than
+    # 1e-3 l_1 is determined to ~u l_1 / gap in FP32, and must match the
+    # oracle's column under the same sign rule
+    for n in (0, 1):
+        Y = tucker.multi_mode_product(T, ref.factors, skip=n, transpose=True)
+        w = np.sort(np.linalg.eigvalsh(tucker.gram(tucker.unfold(Y, n))))[::-1]
+        r = cfg["ranks"][n]
+        sep = [min(w[i - 1] - w[i] if i > 0 else np.inf, w[i] - w[i + 1]) / w[0] for i in range(r)]
+        cols = [i for i in range(r) if sep[i] > 1e-3]
+        dev = [float(np.abs(Us[n][:, i] - ref.factors[n][:, i]).max()) for i in cols]
+        print(f"xga mode {n}: separated columns {cols}, max deviation {max(dev):.2e}")
+        assert len(cols) >= 3 and max(dev) < 2e-3, (n, cols, dev)
     # the quantiser on the GPU core is bit-exact against the oracle's quantiser
     core = res["core"].cpu().numpy().transpose(3, 2, 1, 0)
     q, sc = mes.quantize_core(res["core"], cfg["ranks"], 16)
