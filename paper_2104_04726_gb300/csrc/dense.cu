@@ -1084,13 +1084,29 @@ eig_mid_kernel(const float* __restrict__ Hin, int r, float* __restrict__ Z, cons
 // refinement of Ogita and Aishima, 2018): d_i = S_ii / G_ii,
 //   e_ii = (1 - G_ii) / 2,
 //   e_ij = (S_ij - d_j G_ij) / (d_j - d_i)   (i != j),
-// and where that first-order rotation would not be small (|e_ij| >= 1/2: the
-// two values are too close for the current accuracy of X, including the
-// near-degenerate pairs an FP32 A cannot separate) only the orthonormality
-// part, e_ij = -G_ij / 2, so such a pair stays unrotated.
+// Pairs whose values are closer than kRRCluster of the largest |d| form
+// clusters and keep only the orthonormality part, e_ij = -G_ij / 2 (no
+// rotation between them): an FP32 A resolves its eigenvalues only to about
+// 2^-24 |A|, and the first-order step needs gaps well above that (in a
+// float32 emulation with the 1024x768 scene's spectrum, a floor of 1e-6 made
+// the iteration diverge, 1e-5 lost orthonormality to 3e-2 on the way, 1e-4
+// converged in two or three steps).  A pair whose first-order rotation would
+// not be small (|e_ij| >= 1/2) is treated the same way.
 // --------------------------------------------------------------------------
+constexpr float kRRCluster = 1e-4f;
+
 __global__ void rr_update_kernel(const float* __restrict__ S, const float* __restrict__ G, int r,
                                  float* __restrict__ E) {
+  __shared__ float dmax_s[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
+    m = fmaxf(m, fabsf(S[i + (int64_t)r * i] / G[i + (int64_t)r * i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) dmax_s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float dmax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dmax = fmaxf(dmax, dmax_s[w]);
+  const float floor = kRRCluster * dmax;
   const int64_t n = (int64_t)r * r;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % r), j = (int)(e / r);   // column-major: E[i + r j]
@@ -1102,7 +1118,7 @@ __global__ void rr_update_kernel(const float* __restrict__ S, const float* __res
     const float di = S[i + (int64_t)r * i] / G[i + (int64_t)r * i];
     const float dj = S[j + (int64_t)r * j] / G[j + (int64_t)r * j];
     const float num = S[e] - dj * gij, den = dj - di;
-    E[e] = (fabsf(num) < 0.5f * fabsf(den)) ? num / den : -0.5f * gij;
+    E[e] = (fabsf(den) > floor && fabsf(num) < 0.5f * fabsf(den)) ? num / den : -0.5f * gij;
   }
 }
 
