@@ -11,6 +11,8 @@
 // Yc, B and R (BT.2020 constant luminance).  The squared norm is accumulated
 // in FP64 per thread, reduced per block, and the per-block partials are
 // summed by one block in a fixed order, so the result is reproducible.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace {
@@ -39,18 +41,45 @@ __device__ __forceinline__ float oetf2020_inverse(float e) {
 constexpr int kThreads = 256;
 constexpr int kPix = 8;
 
-// accurate powf (not the fast log2/exp2 pair): the inverse transform must
-// recover the 8-bit input exactly, and the power 1/0.43 of the inverse
-// magnifies forward errors on saturated colours with a dark channel
-__device__ __forceinline__ float signed_pow043(float v) {
-  float a = fabsf(v);
-  float p = (a > 0.f) ? powf(a, 0.43f) : 0.f;
-  return copysignf(p, v);
+// x^0.43 of the IPT cone responses, written for this one exponent (the
+// general powf made the pre-pass issue-bound: three per pixel).  With
+// x = m 2^e, m in [1, 2): x^0.43 = 2^(0.43 e) m^0.43, the first factor from a
+// table over the 254 normal exponents, the second on 16 sub-intervals of
+// [1, 2) as c^0.43 (1 + v)^0.43 with c the sub-interval's centre, v = m/c - 1
+// (|v| <= 1/32) and the binomial series to degree 4 (the first term left out
+// is below 1e-9).  The tables are computed on the host in double precision
+// and rounded once, so the result is within a few ulp of x^0.43: accurate
+// enough that the inverse transform still recovers the 8-bit input exactly
+// (the fast log2/exp2 pair, errors up to 2e-5, did not).  Zero and subnormal
+// inputs (below 2^-126, so x^0.43 < 2^-54) give 0.
+struct Pow043 {
+  float t2[254];                 // 2^(0.43 e), e = -126 .. 127
+  float c[16], ic[16], pc[16];   // sub-interval centres, their reciprocals and 0.43 powers
+  float a[4];                    // binomial coefficients of (1 + v)^0.43, degrees 1 .. 4
+};
+
+struct Pow043Smem {
+  float t2[256], c[16], ic[16], pc[16];
+};
+
+__device__ __forceinline__ float pow043(float x, const Pow043Smem& T, const float (&a)[4]) {
+  const uint32_t u = __float_as_uint(x);
+  const int eb = (int)(u >> 23);   // biased exponent (x >= 0)
+  if (eb == 0) return 0.f;
+  const int j = (int)((u >> 19) & 15u);
+  const float m = __uint_as_float((u & 0x7FFFFFu) | 0x3F800000u);
+  const float v = (m - T.c[j]) * T.ic[j];
+  const float p = fmaf(v, fmaf(v, fmaf(v, fmaf(v, a[3], a[2]), a[1]), a[0]), 1.f);
+  return (T.pc[j] * T.t2[eb - 1]) * p;
+}
+
+__device__ __forceinline__ float signed_pow043(float v, const Pow043Smem& T, const float (&a)[4]) {
+  return copysignf(pow043(fabsf(v), T, a), v);
 }
 
 __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float* lut_lin,
-                                              const float* lut_p, int r8, int g8, int b8,
-                                              float& c0, float& c1, float& c2) {
+                                              const float* lut_p, const Pow043Smem& T, const float (&pa)[4],
+                                              int r8, int g8, int b8, float& c0, float& c1, float& c2) {
   if (P.space == MES_YCBCR601) {
     float r = lut_p[r8], g = lut_p[g8], b = lut_p[b8];
     float y = fmaf(0.299f, r, fmaf(0.587f, g, 0.114f * b));
@@ -72,9 +101,9 @@ __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float
     float L = fmaf(P.a[0], r, fmaf(P.a[1], g, P.a[2] * b));
     float M = fmaf(P.a[3], r, fmaf(P.a[4], g, P.a[5] * b));
     float S = fmaf(P.a[6], r, fmaf(P.a[7], g, P.a[8] * b));
-    L = signed_pow043(L);
-    M = signed_pow043(M);
-    S = signed_pow043(S);
+    L = signed_pow043(L, T, pa);
+    M = signed_pow043(M, T, pa);
+    S = signed_pow043(S, T, pa);
     c0 = fmaf(P.b[0], L, fmaf(P.b[1], M, P.b[2] * S));
     c1 = fmaf(P.b[3], L, fmaf(P.b[4], M, P.b[5] * S));
     c2 = fmaf(P.b[6], L, fmaf(P.b[7], M, P.b[8] * S));
@@ -96,15 +125,23 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourParams P,
+colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourParams P, const Pow043 PT,
               float* __restrict__ out, double* __restrict__ partials) {
   __shared__ float lut_lin[256];
   __shared__ float lut_p[256];
+  __shared__ Pow043Smem T;
   for (int v = threadIdx.x; v < 256; v += blockDim.x) {
     float p = (float)v / 255.0f;
     lut_p[v] = p;
     lut_lin[v] = (P.space != MES_YCBCR601) ? powf(p, P.gamma) : p;
+    T.t2[v] = v < 254 ? PT.t2[v] : 0.f;
+    if (v < 16) {
+      T.c[v] = PT.c[v];
+      T.ic[v] = PT.ic[v];
+      T.pc[v] = PT.pc[v];
+    }
   }
+  const float pa[4] = {PT.a[0], PT.a[1], PT.a[2], PT.a[3]};
   __syncthreads();
 
   double acc = 0.0;
@@ -128,7 +165,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
           int bi = i * 3 + c;
           bytes[c] = (words[bi >> 2] >> ((bi & 3) * 8)) & 0xff;
         }
-        convert_pixel(P, lut_lin, lut_p, bytes[0], bytes[1], bytes[2], o[0][i], o[1][i], o[2][i]);
+        convert_pixel(P, lut_lin, lut_p, T, pa, bytes[0], bytes[1], bytes[2], o[0][i], o[1][i], o[2][i]);
       }
       // the 24 squares of this group summed in FP32, then one FP64 add
       // (the FP64 rate is a small fraction of the FP32 rate on this GPU)
@@ -150,7 +187,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
       const int64_t p = g - k * npix;
       const uint8_t* s = rgb8 + (k * npix + p) * 3;
       float c0, c1, c2;
-      convert_pixel(P, lut_lin, lut_p, s[0], s[1], s[2], c0, c1, c2);
+      convert_pixel(P, lut_lin, lut_p, T, pa, s[0], s[1], s[2], c0, c1, c2);
       out[(3 * k + 0) * npix + p] = c0;
       out[(3 * k + 1) * npix + p] = c1;
       out[(3 * k + 2) * npix + p] = c2;
@@ -369,16 +406,38 @@ unsigned colour_grid(int64_t npix, int64_t K) {
   return grid_for(work, kThreads, (int64_t)sm_count() * 8);
 }
 
+// Tables of pow043, in double precision, rounded once (built on first use).
+const Pow043& pow043_tables() {
+  static const Pow043 T = [] {
+    Pow043 t;
+    for (int i = 0; i < 254; ++i) t.t2[i] = (float)std::exp2(0.43 * (double)(i + 1 - 127));
+    for (int j = 0; j < 16; ++j) {
+      const double c = 1.0 + (j + 0.5) / 16.0;
+      t.c[j] = (float)c;   // exact
+      t.ic[j] = (float)(1.0 / c);
+      t.pc[j] = (float)std::pow(c, 0.43);
+    }
+    double coef = 1.0;
+    for (int k = 1; k <= 4; ++k) {
+      coef *= (0.43 - (k - 1)) / k;   // generalised binomial coefficient C(0.43, k)
+      t.a[k - 1] = (float)coef;
+    }
+    return t;
+  }();
+  return T;
+}
+
 mes_status colour_launch(const uint8_t* rgb8, int64_t s1, int64_t s2, int64_t K, int space,
                          float gamma, float* out, double* partials, double* norm2,
                          cudaStream_t st) {
   ColourParams P;
   make_params(space, gamma, &P);
+  const Pow043& PT = pow043_tables();
   const int64_t npix = s1 * s2;
   unsigned grid = colour_grid(npix, K);
   {
   ProfScope prof("colour", st, 0.0, 15.0 * npix * K);
-  colour_kernel<<<grid, kThreads, 0, st>>>(rgb8, npix, K, P, out, norm2 ? partials : nullptr);
+  colour_kernel<<<grid, kThreads, 0, st>>>(rgb8, npix, K, P, PT, out, norm2 ? partials : nullptr);
   MES_LAUNCH_CHECK();
   }
   if (norm2) {

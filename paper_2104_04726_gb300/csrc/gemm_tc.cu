@@ -19,10 +19,12 @@
 // product), so the result has FP32-level accuracy.  KIND 3, the six-term
 // BF16 split: each operand is stored as three BF16 parts x = x1 + x2 + x3
 // (24 significant bits, as many as FP32) in the K_hi planes of its tensor
-// map, and the K walk runs over the part pairs (1,1) (1,2) (2,1) (1,3) (3,1)
-// (2,2) -- every product down to 2^-16 of the leading one -- into one FP32
-// accumulator, so the result has FP32-level accuracy at BF16 tensor-core
-// rate (used for the Grams of the factor update).  Split-K over
+// map; each K slice stages the three parts of both operands and issues the
+// part pairs (1,1) (1,2) (2,1) (1,3) (3,1) (2,2) -- every product down to
+// 2^-16 of the leading one -- the leading pair into one FP32 accumulator and
+// the corrections into a second, summed in the epilogue, so the result has
+// FP32-level accuracy at BF16 tensor-core rate (used for the Grams of the
+// factor update).  Split-K over
 // grid.z writes FP32 partial tiles that one fixed-order pass reduces, so the
 // result is deterministic.  Every mbarrier wait is bounded (globaltimer,
 // 2 s unless the caller sets a shorter bound); a timeout sets an error bit.
@@ -531,7 +533,10 @@ template <int KIND, int BN, int STAGES, int CTAS = 1>
 struct PCfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
+  // KIND 3 stages the three parts of both operands of a K slice together:
+  // A1 A2 A3 B1 B2 B3, each loaded once and read by the six pair products
+  static constexpr int PARTS = KIND == 3 ? 3 : 1;
+  static constexpr int STAGE = PARTS * (A_BYTES + B_BYTES);
   static constexpr int EPI = kEpiWarps * 32 * 33 * 4;   // per-warp transpose tiles (own region)
   static constexpr int BAR = 8 * (2 * STAGES + 5);
   static constexpr int SMEM = STAGES * STAGE + EPI + 1024 /*align*/ + BAR + 16;
@@ -628,12 +633,20 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
         const int kh = kt / args.k_tiles_lo;
         const int kl = (kt - kh * args.k_tiles_lo) * (128 / kind_bytes(KIND));
-        // KIND 3: K block kh is part pair kh; the parts are the K_hi planes
-        const int kha = KIND == 3 ? pair_a(kh) : kh, khb = KIND == 3 ? pair_b(kh) : kh;
         uint8_t* sa = ring + stage * C::STAGE;
         mbar_expect_tx(&full[stage], (uint32_t)C::STAGE);
-        tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kha, args.a_batched ? b : 0);
-        tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, khb, args.b_batched ? b : 0);
+        if (KIND == 3) {
+          // the three parts (K_hi planes) of A, then of B
+#pragma unroll
+          for (int part = 0; part < 3; ++part) {
+            tma_load_4d(sa + part * C::A_BYTES, &mapA, &full[stage], kl, (int)m0, part, args.a_batched ? b : 0);
+            tma_load_4d(sa + 3 * C::A_BYTES + part * C::B_BYTES, &mapB, &full[stage], kl, (int)n0, part,
+                        args.b_batched ? b : 0);
+          }
+        } else {
+          tma_load_4d(sa, &mapA, &full[stage], kl, (int)m0, kh, args.a_batched ? b : 0);
+          tma_load_4d(sa + C::A_BYTES, &mapB, &full[stage], kl, (int)n0, kh, args.b_batched ? b : 0);
+        }
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
@@ -663,9 +676,6 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       tc_fence_after();
       const uint32_t d0 = tmem + (uint32_t)(acc * C::ACC_COLS);
-      // KIND 3: the leading pair (1,1) into d0, the five correction pairs
-      // into d0 + BN, so the small terms are not rounded against the full sum
-      const int k_lead = KIND == 3 ? args.k_tiles_lo : 1 << 30;
       for (int kt = kb; kt < ke; ++kt) {
         if (!mbar_wait(&full[stage], phase, wait_ns)) {
           ok = false;
@@ -673,14 +683,26 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
         tc_fence_after();
         const uint32_t sa = smem_u32(ring + stage * C::STAGE);
-        const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + C::A_BYTES);
-        const bool lead = kt < k_lead;
-        const uint32_t d = lead ? d0 : d0 + BN;
-        // first K slice of this accumulator in the tile's range: overwrite
-        const bool first = lead ? kt == kb : kt == (kb > k_lead ? kb : k_lead);
+        if (KIND == 3) {
+          // the six part pairs: the leading pair (1,1) into d0, the five
+          // correction pairs into d0 + BN, so the small terms are not rounded
+          // against the full sum
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma<KIND>(d, da + 2 * kk, db + 2 * kk, C::IDESC, (!first || kk > 0) ? 1u : 0u);
+          for (int q = 0; q < 6; ++q) {
+            const uint64_t da = sw128_desc(sa + pair_a(q) * C::A_BYTES);
+            const uint64_t db = sw128_desc(sa + 3 * C::A_BYTES + pair_b(q) * C::B_BYTES);
+            const uint32_t d = q == 0 ? d0 : d0 + BN;
+            const bool first = kt == kb && q <= 1;   // first slice of each accumulator: overwrite
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma<KIND>(d, da + 2 * kk, db + 2 * kk, C::IDESC, (!first || kk > 0) ? 1u : 0u);
+          }
+        } else {
+          const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + C::A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma<KIND>(d0, da + 2 * kk, db + 2 * kk, C::IDESC, (kt > kb || kk > 0) ? 1u : 0u);
+        }
         mma_commit(&empty[stage]);
         if (++stage == STAGES) {
           stage = 0;
@@ -714,9 +736,11 @@ tcp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         break;
       }
       tc_fence_after();
-      // KIND 3: which of the tile's two accumulators its K range wrote
-      const bool has_lead = KIND != 3 || kb < args.k_tiles_lo;
-      const bool has_corr = KIND == 3 && ke > args.k_tiles_lo;
+      // KIND 3: every K slice writes both accumulators
+      const bool has_lead = true;
+      const bool has_corr = KIND == 3;
+      (void)kb;
+      (void)ke;
       const uint32_t row = (uint32_t)(wq * 32) << 16;
       for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
         uint32_t v[32];
@@ -899,9 +923,8 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
   a.M = g.M;
   a.N = g.N;
   a.k_tiles_lo = (int)((g.K_lo + BK - 1) / BK);
-  // KIND 3: the K_hi planes are the three parts and the walk runs over six
-  // part pairs
-  a.k_tiles_total = a.k_tiles_lo * (kind == 3 ? 6 : (int)g.K_hi);
+  // KIND 3: the K_hi planes are the three parts, all staged with each K slice
+  a.k_tiles_total = a.k_tiles_lo * (kind == 3 ? 1 : (int)g.K_hi);
   a.lower = g.lower ? 1 : 0;
   a.Cp = g.Cp;
   a.cp_plane = g.cp_plane;
@@ -964,7 +987,7 @@ mes_status gemm_tc_cfg(const mes::Gemm& g, int kind, int bn, int want_splits, fl
     if (kind == 3 && (rs || g.accumulate || ntiles >= INT32_MAX))
       return fail(MES_ERR_INVALID_ARG, "gemm_tc: the six-term product has no residual or accumulate mode");
     if (kind == 3) {
-      MES_TRY((launch_tcp<3, 128, 6>(ma, mb, a, mt, nt, (int)ntiles, st)));
+      MES_TRY((launch_tcp<3, 128, 2>(ma, mb, a, mt, nt, (int)ntiles, st)));
     } else if (pv && kind != 2 && !rs && !g.accumulate && ntiles < INT32_MAX && (pv == 1 || bn == 128)) {
       // persistent kernel: tiles looped per CTA, double-buffered accumulator
       if (pv == 2) {
@@ -1071,7 +1094,7 @@ mes_status gemm_tc(const Gemm& g, int kind, float* split_ws, int64_t split_ws_el
   }
   // candidates: both tile widths (one for KIND 2) x split-K 1..16 (>= 4 K-tiles a split)
   const int BK = 128 / kind_bytes(kind);
-  const int64_t kt = ((g.K_lo + BK - 1) / BK) * (kind == 3 ? 6 : g.K_hi);
+  const int64_t kt = ((g.K_lo + BK - 1) / BK) * (kind == 3 ? 1 : g.K_hi);
   cudaEvent_t e0, e1;
   MES_CUDA_TRY(cudaEventCreate(&e0));
   MES_CUDA_TRY(cudaEventCreate(&e1));

@@ -42,26 +42,32 @@ plane_absmax_kernel(const float* __restrict__ core, int64_t plane_size, int64_t 
   }
 }
 
+// Grid (chunks of a plane, planes): the plane comes from blockIdx.y, so no
+// element needs an integer division, and the plane's scale is one FP32
+// division per thread rather than per element (the same IEEE operation, so
+// the codes do not change).
 __global__ void __launch_bounds__(kThreads)
-quantize_kernel(const float* __restrict__ core, int64_t plane_size, int64_t total,
+quantize_kernel(const float* __restrict__ core, int64_t plane_size, int64_t chunk,
                 const unsigned* __restrict__ maxbits, float qmax, int16_t* __restrict__ q,
                 float* __restrict__ scales) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t p = i / plane_size;
-    const float m = __uint_as_float(maxbits[p]);
+  const int64_t p = blockIdx.y;
+  const int64_t begin = (int64_t)blockIdx.x * chunk;
+  int64_t end = begin + chunk;
+  if (end > plane_size) end = plane_size;
+  const float m = __uint_as_float(maxbits[p]);
+  const float scale = (m != 0.f) ? __fdiv_rn(m, qmax) : 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) scales[p] = scale;
+  const float* src = core + p * plane_size;
+  int16_t* dst = q + p * plane_size;
+  const int iq = (int)qmax;
+  for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
     int16_t code = 0;
-    float scale = 0.f;
     if (m != 0.f) {
-      scale = __fdiv_rn(m, qmax);
-      float v = __fdiv_rn(core[i], scale);
-      int c = __float2int_rn(v);
-      int iq = (int)qmax;
+      int c = __float2int_rn(__fdiv_rn(__ldg(src + i), scale));
       c = c > iq ? iq : (c < -iq ? -iq : c);
       code = (int16_t)c;
     }
-    q[i] = code;
-    if (i - p * plane_size == 0) scales[p] = scale;
+    dst[i] = code;
   }
 }
 
@@ -117,9 +123,14 @@ mes_status quantize_launch(const float* core, int64_t plane_size, int64_t planes
   }
   const int64_t total = plane_size * planes;
   const float qmax = (float)((1 << (bits - 1)) - 1);
+  // enough chunks per plane to give every SM a few blocks
+  int64_t qchunk = (total + (int64_t)sm_count() * 8 - 1) / ((int64_t)sm_count() * 8);
+  qchunk = ((qchunk + kThreads - 1) / kThreads) * kThreads;
+  if (qchunk < kThreads) qchunk = kThreads;
+  if (qchunk > plane_size) qchunk = ((plane_size + kThreads - 1) / kThreads) * kThreads;
+  dim3 g2((unsigned)((plane_size + qchunk - 1) / qchunk), (unsigned)planes);
   ProfScope prof("quantize", st, 0.0, 6.0 * total + 4.0 * planes);
-  quantize_kernel<<<grid_for(total, kThreads, (int64_t)sm_count() * 16), kThreads, 0, st>>>(
-      core, plane_size, total, maxbits, qmax, q, scales);
+  quantize_kernel<<<g2, kThreads, 0, st>>>(core, plane_size, qchunk, maxbits, qmax, q, scales);
   MES_LAUNCH_CHECK();
   return MES_OK;
 }
