@@ -1060,8 +1060,11 @@ bool tuning_on() {
 
 std::string tune_key(const mes::Gemm& g, int kind) {
   char buf[200];
-  snprintf(buf, sizeof buf, "k%d m%lld n%lld kl%lld kh%lld b%d ab%d bb%d", kind, (long long)g.M, (long long)g.N,
-           (long long)g.K_lo, (long long)g.K_hi, g.batch, g.a_b != 0 ? 1 : 0, g.b_b != 0 ? 1 : 0);
+  // the CTA share (concurrency hint) is part of the key: a choice tuned for
+  // a product alone is not the one for a product sharing the GPU
+  snprintf(buf, sizeof buf, "k%d m%lld n%lld kl%lld kh%lld b%d ab%d bb%d f%lld", kind, (long long)g.M,
+           (long long)g.N, (long long)g.K_lo, (long long)g.K_hi, g.batch, g.a_b != 0 ? 1 : 0, g.b_b != 0 ? 1 : 0,
+           (long long)g.fill);
   return buf;
 }
 

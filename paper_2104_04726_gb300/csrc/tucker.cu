@@ -52,7 +52,7 @@ using mes::KronDesc;
 constexpr float kShiftZ = 1e-5f;
 constexpr float kShiftW = 1e-5f;
 // Refinement steps of the Rayleigh-Ritz rotation for ranks above 128.
-constexpr int kRRSteps = 4;
+constexpr int kRRSteps = 3;
 
 struct Shape {
   int N = 0;
@@ -880,6 +880,13 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     if (any_full) MES_TRY(core_from_B(nullptr));
   }
 
+  // The end of the decomposition (the extra CholeskyQR pass, the canonical
+  // basis, the fit) is a short chain of small products run once: its
+  // CUDA-core products split over all SMs whatever the concurrency hint
+  // (un-split, the 384 x 384 core Gram took 1.1 ms on nine CTAs against
+  // ~30 us split, and more SM time, not less).
+  d.fill = 0;
+
   // ---- one more CholeskyQR pass on each large factor ----
   // The sweeps orthonormalise with one pass (enough for the iteration); the
   // returned factors get a second one, S <- S R^-1, and the core follows
@@ -924,7 +931,8 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
         // eigenvectors) leaves H nearly diagonal, and X <- X (I + E) with E
         // from rr_update converges from X = I (quadratically once the
         // rotations are small); pairs closer than the current accuracy stay
-        // unrotated.  Four steps of four r x r products each.
+        // unrotated.  Three steps of four r x r products each (a float32
+        // emulation with the 1024x768 scene's spectrum converged in two).
         float *Gm = rrw, *HX = rrw + r * r, *Sm = rrw + 2 * r * r, *E = rrw + 3 * r * r, *Xn = rrw + 4 * r * r;
         float* Xc = d.cwX;
         MES_TRY(mes::identity_fill(Xc, r, (int)r, st));
