@@ -446,23 +446,28 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 // restart together.
 // --------------------------------------------------------------------------
 constexpr int kDsmMaxR = 512;
+constexpr int kDsm4MaxR = 480;
 static_assert(kChol == 256, "the diagonal-block update maps 8 warps to 32 columns");
 constexpr int LD = PB + 1;
 
+template <int CL>
 __device__ __forceinline__ int dsm_slot_offset(int rank, int slot, int rp) {
   int off = 0;
-  for (int q = 0; q < slot; ++q) off += rp - PB * (rank + kCL * q);
+  for (int q = 0; q < slot; ++q) off += rp - PB * (rank + CL * q);
   return off;  // rows
 }
 
-__host__ __device__ inline size_t chol_dsm_smem(int r) {
+__host__ __device__ inline size_t chol_dsm_smem(int r, int cl) {
   const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
   int rows = 0;  // CTA 0 holds the most rows
-  for (int k = 0; k < nb; k += kCL) rows += rp - PB * k;
+  for (int k = 0; k < nb; k += cl) rows += rp - PB * k;
   return (size_t)((rows + rp) * LD + rp + 8) * sizeof(float);
 }
 
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kChol, 1)
+// CL CTAs in the cluster: 8 for r <= kDsmMaxR, 4 (half the SMs) while the
+// owned columns still fit in one CTA's shared memory (r <= kDsm4MaxR)
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kChol, 1)
 chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
                 float* __restrict__ dinv_out, float* __restrict__ Linv_blk, int* __restrict__ flags,
                 const int* __restrict__ skip, int* __restrict__ clean) {
@@ -479,7 +484,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
   float* dinv = smem;              // rp
   float* store = dinv + rp;        // owned block columns
   int store_rows = 0;
-  for (int k = rank; k < nb; k += kCL) store_rows += rp - PB * k;
+  for (int k = rank; k < nb; k += CL) store_rows += rp - PB * k;
   // panel rows read from L (row stride 33)
   float* Pl_alloc = smem + rp + store_rows * LD;
   // bad-pivot flags per attempt and step parity; CTA 0's copy is the
@@ -573,7 +578,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     const float floor = fmaxf(1e-7f, 0.1f * shift);
     if (t == 0) lbad = 0;
     // owned columns of A = D^-1 M D^-1 + shift I (lower part; rows >= r zero)
-    for (int k = rank, off = 0; k < nb; off += rp - PB * k, k += kCL) {
+    for (int k = rank, off = 0; k < nb; off += rp - PB * k, k += CL) {
       const int h = rp - PB * k;
       float* Sk = store + off * LD;
       for (int e = t; e < h * PB; e += kChol) {
@@ -601,14 +606,14 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     for (int p = 0; p < nb - 1; ++p) {
       if (bad0[2 * attempt + ((p - 1) & 1)]) { failed = true; break; }
       int kmin = rank;
-      while (kmin <= p) kmin += kCL;
+      while (kmin <= p) kmin += CL;
       if (kmin < nb) {
         // panel p, rows g_lo .. rp-1: the owner uses its own copy, the
         // others read it from L (column-major, written before the barrier)
-        const int owner = p % kCL, g_lo = PB * kmin;
+        const int owner = p % CL, g_lo = PB * kmin;
         const float* P;
         if (owner == rank) {
-          P = store + (dsm_slot_offset(rank, p / kCL, rp) + (g_lo - PB * p)) * LD;
+          P = store + (dsm_slot_offset<CL>(rank, p / CL, rp) + (g_lo - PB * p)) * LD;
         } else {
           const int nrows = rp - g_lo;
           const float* Lp = Lout + (int64_t)r * (PB * p) + g_lo;
@@ -623,8 +628,8 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
           P = Pl_alloc;
         }
         __syncthreads();
-        int slot = (kmin - rank) / kCL;
-        int off = dsm_slot_offset(rank, slot, rp);
+        int slot = (kmin - rank) / CL;
+        int off = dsm_slot_offset<CL>(rank, slot, rp);
         if (kmin == p + 1) {
           // look-ahead on the next column: its diagonal block is updated
           // first and factored by warp 0 while warps 1..7 update the rows
@@ -656,9 +661,9 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
           publish(Sk, kmin);
           if (t == 0 && lbad) bad0[2 * attempt + (p & 1)] = 1;
           off += h;
-          kmin += kCL;
+          kmin += CL;
         }
-        for (int k = kmin; k < nb; off += rp - PB * k, k += kCL)
+        for (int k = kmin; k < nb; off += rp - PB * k, k += CL)
           update_col(store + off * LD, k, P, g_lo, 0, rp - PB * k, 0, kChol / 32);
       }
       cluster.sync();
@@ -677,7 +682,7 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
   if (clean && rank == 0 && t == 0) *clean = restarts == 0;
   // L is already in place (each column written when factored); the inverses
   // of the owned diagonal blocks, one warp each
-  for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += kCL, ++q)
+  for (int k = rank, off = 0, q = 0; k < nb; off += rp - PB * k, k += CL, ++q)
     if (warp == q) warp_tri_inv32(store + off * LD, Linv_blk + (size_t)k * PB * PB);
 }
 
@@ -1162,16 +1167,24 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
   }
   static int dsm_ok = -1;
   if (dsm_ok < 0) {
-    cudaError_t e = cudaFuncSetAttribute(chol_dsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)chol_dsm_smem(kDsmMaxR));
+    cudaError_t e = cudaFuncSetAttribute(chol_dsm_kernel<kCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_dsm_smem(kDsmMaxR, kCL));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(chol_dsm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)chol_dsm_smem(kDsm4MaxR, 4));
     dsm_ok = (e == cudaSuccess) ? 1 : 0;
     if (e != cudaSuccess && getenv("MES_DEBUG"))
       fprintf(stderr, "[mes] shared-memory cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
     cudaGetLastError();
   }
+  static const bool cl8 = getenv("MES_CHOL_CL8") != nullptr;   // measurement switch: always 8 CTAs
   if (r > 128 && r <= kDsmMaxR && dsm_ok == 1) {
-    chol_dsm_kernel<<<kCL, kChol, chol_dsm_smem(r), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip,
-                                                           clean);
+    if (r <= kDsm4MaxR && !cl8)
+      chol_dsm_kernel<4><<<4, kChol, chol_dsm_smem(r, 4), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip,
+                                                                 clean);
+    else
+      chol_dsm_kernel<kCL><<<kCL, kChol, chol_dsm_smem(r, kCL), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags,
+                                                                       skip, clean);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return MES_OK;
     if (getenv("MES_DEBUG"))
