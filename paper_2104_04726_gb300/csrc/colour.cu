@@ -54,27 +54,27 @@ constexpr int kPix = 8;
 // inputs (below 2^-126, so x^0.43 < 2^-54) give 0.
 struct Pow043 {
   float t2[254];                 // 2^(0.43 e), e = -126 .. 127
-  float c[16], ic[16], pc[16];   // sub-interval centres, their reciprocals and 0.43 powers
+  float ic[16], pc[16];          // 1 / c and c^0.43 for the sub-interval centres c = 1 + (j + 1/2)/16
   float a[4];                    // binomial coefficients of (1 + v)^0.43, degrees 1 .. 4
 };
 
 struct Pow043Smem {
-  float t2[256], c[16], ic[16], pc[16];
+  float t2[256];
+  float2 icpc[16];               // (1 / c, c^0.43) per sub-interval
 };
 
+// x >= 0 (zero, subnormals and a negative zero give 0)
 __device__ __forceinline__ float pow043(float x, const Pow043Smem& T, const float (&a)[4]) {
   const uint32_t u = __float_as_uint(x);
-  const int eb = (int)(u >> 23);   // biased exponent (x >= 0)
-  if (eb == 0) return 0.f;
+  const int eb = (int)(u >> 23);   // biased exponent
+  if (eb == 0 || eb > 254) return 0.f;
   const int j = (int)((u >> 19) & 15u);
   const float m = __uint_as_float((u & 0x7FFFFFu) | 0x3F800000u);
-  const float v = (m - T.c[j]) * T.ic[j];
+  const float c = fmaf((float)j, 1.f / 16.f, 1.f + 1.f / 32.f);   // exact
+  const float2 t = T.icpc[j];
+  const float v = (m - c) * t.x;
   const float p = fmaf(v, fmaf(v, fmaf(v, fmaf(v, a[3], a[2]), a[1]), a[0]), 1.f);
-  return (T.pc[j] * T.t2[eb - 1]) * p;
-}
-
-__device__ __forceinline__ float signed_pow043(float v, const Pow043Smem& T, const float (&a)[4]) {
-  return copysignf(pow043(fabsf(v), T, a), v);
+  return (t.y * T.t2[eb - 1]) * p;
 }
 
 __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float* lut_lin,
@@ -101,9 +101,12 @@ __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float
     float L = fmaf(P.a[0], r, fmaf(P.a[1], g, P.a[2] * b));
     float M = fmaf(P.a[3], r, fmaf(P.a[4], g, P.a[5] * b));
     float S = fmaf(P.a[6], r, fmaf(P.a[7], g, P.a[8] * b));
-    L = signed_pow043(L, T, pa);
-    M = signed_pow043(M, T, pa);
-    S = signed_pow043(S, T, pa);
+    // every entry of the linear-sRGB -> LMS matrix is positive (the product
+    // of the published XYZ and cone matrices), so the cone responses of
+    // 8-bit input are >= 0; the clamp only absorbs a rounding to -0
+    L = pow043(fmaxf(L, 0.f), T, pa);
+    M = pow043(fmaxf(M, 0.f), T, pa);
+    S = pow043(fmaxf(S, 0.f), T, pa);
     c0 = fmaf(P.b[0], L, fmaf(P.b[1], M, P.b[2] * S));
     c1 = fmaf(P.b[3], L, fmaf(P.b[4], M, P.b[5] * S));
     c2 = fmaf(P.b[6], L, fmaf(P.b[7], M, P.b[8] * S));
@@ -135,11 +138,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
     lut_p[v] = p;
     lut_lin[v] = (P.space != MES_YCBCR601) ? powf(p, P.gamma) : p;
     T.t2[v] = v < 254 ? PT.t2[v] : 0.f;
-    if (v < 16) {
-      T.c[v] = PT.c[v];
-      T.ic[v] = PT.ic[v];
-      T.pc[v] = PT.pc[v];
-    }
+    if (v < 16) T.icpc[v] = make_float2(PT.ic[v], PT.pc[v]);
   }
   const float pa[4] = {PT.a[0], PT.a[1], PT.a[2], PT.a[3]};
   __syncthreads();
@@ -412,8 +411,7 @@ const Pow043& pow043_tables() {
     Pow043 t;
     for (int i = 0; i < 254; ++i) t.t2[i] = (float)std::exp2(0.43 * (double)(i + 1 - 127));
     for (int j = 0; j < 16; ++j) {
-      const double c = 1.0 + (j + 0.5) / 16.0;
-      t.c[j] = (float)c;   // exact
+      const double c = 1.0 + (j + 0.5) / 16.0;   // exactly representable
       t.ic[j] = (float)(1.0 / c);
       t.pc[j] = (float)std::pow(c, 0.43);
     }

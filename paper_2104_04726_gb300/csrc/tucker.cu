@@ -187,7 +187,6 @@ struct Driver {
   // makes A can write its BF16 parts to gparts (Gemm::Cp) instead of a split
   // pass over A.
   bool gram_tc(int64_t s) const { return tc() && gparts && s % 8 == 0; }
-  bool fuse_parts = getenv("MES_NO_FUSED_PARTS") == nullptr;
 
   // parts_ready: A's three BF16 parts are already in gparts (written by the
   // product that made A)
@@ -267,7 +266,7 @@ struct Driver {
     gz.B = z16 ? reinterpret_cast<const float*>(S16) : (tc() ? Srnd : S); gz.b_n = s; gz.b_k = 1;
     gz.C = Z; gz.c_m = 1; gz.c_n = J;
     // the Gram's BF16 parts straight from the product's epilogue
-    const bool zparts = fuse_parts && gram_tc(J) && (z16 || mes::tc_eligible(gz, 0));
+    const bool zparts = gram_tc(J) && (z16 || mes::tc_eligible(gz, 0));
     if (zparts) { gz.Cp = gparts; gz.cp_plane = J * r; }
     MES_TRY(z16 ? big16(gz) : big(gz));
     // H = Z^T Z, R_z, Zh = Z R_z^-1
@@ -282,11 +281,11 @@ struct Driver {
     if (w16) {
       MES_TRY(mes::to_bf16(Zh, Zh16, J * r, skip, st));
       gw.B = reinterpret_cast<const float*>(Zh16);
-      wparts = fuse_parts && gram_tc(s);
+      wparts = gram_tc(s);
       if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big16(gw));
     } else {
-      wparts = fuse_parts && gram_tc(s) && mes::tc_eligible(gw, 0);
+      wparts = gram_tc(s) && mes::tc_eligible(gw, 0);
       if (wparts) { gw.Cp = gparts; gw.cp_plane = s * r; }
       MES_TRY(big(gw));
     }
