@@ -472,7 +472,7 @@ def measure_serving(mes, dev, precision, rate_cap, seconds, warm_s, fp32_seconds
     return out
 
 
-def measure_batch(mes, dev, precision, n_stacks, seed):
+def measure_batch(mes, dev, precision, n_stacks, seed, streams=16):
     """Batched form: n_stacks stacks of the mixed workload (640x480, 1280x720
     or 1920x1080; 3..7 exposures per view; ranks 20% of the two image modes,
     full rank for colour and view x exposure; IPT or Y'CbCr; 20 sweeps;
@@ -509,7 +509,7 @@ def measure_batch(mes, dev, precision, n_stacks, seed):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 2
     with torch.cuda.stream(st):
-        b = mes.Batch(16)
+        b = mes.Batch(streams)
         b.run(probs)                  # one-time setup outside the capture
         st.synchronize()
         b.capture(probs, stream=st)
@@ -536,7 +536,7 @@ def measure_batch(mes, dev, precision, n_stacks, seed):
         b1.close()
     f32 = [float(p.fit) for p in p32]
     dev_rel = max(abs(a - c) / abs(c) for a, c in zip(fits, f32))
-    return {"stacks": n_stacks, "precision": precision, "graph": True, "internal_streams": 16,
+    return {"stacks": n_stacks, "precision": precision, "graph": True, "internal_streams": streams,
             "stacks_per_s": n_stacks / t_batch, "ms_per_batch": 1e3 * t_batch,
             "fp32_sequential_stacks_per_s": n_stacks / t_seq, "speedup_vs_fp32_sequential": t_seq / t_batch,
             "max_rel_fit_dev_vs_fp32": dev_rel,
@@ -564,6 +564,7 @@ def main():
                     help="Poisson arrival rate of the serving form (capped at 80%% of the measured capacity)")
     ap.add_argument("--batch-stacks", type=int, default=64,
                     help="stacks of the batched-form measurement (0 = skip it)")
+    ap.add_argument("--batch-streams", type=int, default=16, help="internal streams of the batched form")
     ap.add_argument("--concurrency", type=int, default=None,
                     help="concurrency hint of every decomposition (default: --stacks, the stacks run side by "
                          "side; 1: each as if alone, split-K fills all SMs)")
@@ -784,7 +785,8 @@ def main():
                                  "speedup": res["value"] / fp32["value"], "max_rel_fit_dev": dev_rel,
                                  "clocks": fp32["clocks"]}
         if args.batch_stacks > 0 and world == 1:
-            line["batch"] = measure_batch(mes, dev, args.precision, args.batch_stacks, seed=11)
+            line["batch"] = measure_batch(mes, dev, args.precision, args.batch_stacks, seed=11,
+                                          streams=args.batch_streams)
         if args.serve_seconds > 0 and world == 1:
             line["serve"] = measure_serving(mes, dev, args.precision, args.serve_rate, args.serve_seconds,
                                             args.serve_warmup, args.serve_fp32_seconds, seed=7, slots=8,
