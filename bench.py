@@ -565,6 +565,8 @@ def main():
     ap.add_argument("--batch-stacks", type=int, default=64,
                     help="stacks of the batched-form measurement (0 = skip it)")
     ap.add_argument("--batch-streams", type=int, default=16, help="internal streams of the batched form")
+    ap.add_argument("--enqueue-threads", type=int, default=8,
+                    help="host threads enqueueing the stacks of an eager (e2e) step")
     ap.add_argument("--concurrency", type=int, default=None,
                     help="concurrency hint of every decomposition (default: --stacks, the stacks run side by "
                          "side; 1: each as if alone, split-K fills all SMs)")
@@ -655,13 +657,30 @@ def main():
     stacks = [Stack(i) for i in range(S)]
     main_stream = torch.cuda.current_stream()
 
-    def step(precision, e2e=False, main=None):
+    # host threads that enqueue the stacks of an eager step side by side (the
+    # library's calls are thread-safe on separate streams and release the
+    # GIL): ~1100 launches per stack are too many for one enqueueing thread
+    enqueue_threads = max(1, min(S, args.enqueue_threads))
+    pool = None
+    if enqueue_threads > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        pool = ThreadPoolExecutor(max_workers=enqueue_threads, initializer=lambda: torch.cuda.set_device(dev))
+
+    def step(precision, e2e=False, main=None, threaded=False):
         main = main_stream if main is None else main
         start = torch.cuda.Event()
         start.record(main)
         for st_ in stacks:
             st_.stream.wait_event(start)
-            st_.run(precision, e2e)
+        if threaded and pool is not None:
+            def work(i0):
+                for st_ in stacks[i0::enqueue_threads]:
+                    st_.run(precision, e2e)
+            for f in [pool.submit(work, i) for i in range(enqueue_threads)]:
+                f.result()
+        else:
+            for st_ in stacks:
+                st_.run(precision, e2e)
         for st_ in stacks:
             main.wait_stream(st_.stream)
 
@@ -689,7 +708,7 @@ def main():
             if graph is not None:
                 graph.replay()
             else:
-                step(precision, e2e)
+                step(precision, e2e, threaded=True)
         b.record(main_stream)
         torch.cuda.synchronize()
         return slowest_rank_ms(a.elapsed_time(b), dist, dev)
@@ -735,8 +754,9 @@ def main():
         out["fams"] = fams
         out["launches_per_step"] = S * sum(f["launches"] for f in fams) // prof_stacks
         out["prof_stacks"] = prof_stacks
-        # end to end through the public API with host buffers
-        step(precision, True)
+        # end to end through the public API with host buffers, the stacks
+        # enqueued by several host threads
+        step(precision, True, threaded=True)
         torch.cuda.synchronize()
         e2e_ms = timed(args.steps, precision, e2e=True)
         out["e2e"] = whole_job_rate(S, args.steps, world, e2e_ms)
@@ -766,7 +786,7 @@ def main():
                 "data": "synthetic",
                 "config": dict(_config(name, cfg, dims, ranks, args.precision, S, world), concurrency_hint=conc,
                                launch="value: the step captured once as a CUDA graph and replayed; "
-                                      "e2e: eager API calls"),
+                                      f"e2e: eager API calls from {enqueue_threads} host threads"),
                 "roofline": roof, "rooflines": _family_rooflines(res["fams"], peaks, peak_src, sms),
                 "rooflines_note": (f"per kernel family from a profiled pass of {res['prof_stacks']} stacks run one "
                                    "after another (CUDA events on the launch stream, no other work on the GPU): "
@@ -795,6 +815,8 @@ def main():
             cb = cpu_baseline(1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.shutdown()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
