@@ -13,6 +13,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <future>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -270,6 +271,11 @@ struct mes_server {
   // the slot's completion event has fired
   int* dev_status = nullptr;
   int* host_status = nullptr;
+  // per slot: the host task enqueueing the admitted request (its launches
+  // are issued off the admission thread, so admission and retirement go on
+  // while a large request is being enqueued)
+  std::vector<std::future<mes_status>> slot_enq;
+  std::vector<char> slot_enqueuing;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;
@@ -299,11 +305,23 @@ void serve_loop(mes_server* s) {
     for (size_t k = 0; k < s->slots.size(); ++k) {
       const uint64_t id = s->slot_req[k];
       if (!id) continue;
-      cudaError_t q = cudaEventQuery(s->slot_done[k]);
-      if (q == cudaErrorNotReady) continue;
+      mes_status enq = MES_OK;
+      if (s->slot_enqueuing[k]) {
+        // still enqueueing, or just done: the task's status decides
+        if (s->slot_enq[k].wait_for(std::chrono::seconds(0)) != std::future_status::ready) continue;
+        enq = s->slot_enq[k].get();
+        s->slot_enqueuing[k] = 0;
+      }
+      cudaError_t q = cudaSuccess;
+      if (enq == MES_OK) {
+        q = cudaEventQuery(s->slot_done[k]);
+        if (q == cudaErrorNotReady) continue;
+      }
       Request& r = s->reqs[id];
       r.done = true;
-      if (q != cudaSuccess) {
+      if (enq != MES_OK) {
+        r.status = enq;
+      } else if (q != cudaSuccess) {
         cudaGetLastError();
         r.status = MES_ERR_CUDA;
       } else if (s->host_status[k] != MES_OK) {
@@ -362,25 +380,25 @@ void serve_loop(mes_server* s) {
       prob.opts.status = dstat;
       s->host_status[k] = MES_OK;
       if (s->first_admit < 0) s->first_admit = secs(s->t0, Clock::now());
-      lk.unlock();
-      mes_status st = problem_enqueue(prob, s->slots[k]);
-      if (st == MES_OK && (cudaMemcpyAsync(s->host_status + k, dstat, sizeof(int), cudaMemcpyDeviceToHost,
-                                           s->slots[k]) != cudaSuccess ||
-                           cudaEventRecord(s->slot_done[k], s->slots[k]) != cudaSuccess)) {
-        cudaGetLastError();
-        st = MES_ERR_CUDA;
-      }
-      if (st != MES_OK) cudaStreamSynchronize(s->slots[k]);   // let what was enqueued finish
-      lk.lock();
-      if (st != MES_OK) {
-        r.done = true;
-        r.status = st;
-        r.latency_ms = 1e3 * secs(r.submitted, Clock::now());
-        s->slot_req[k] = 0;
-        s->in_use -= r.bytes;
-        ++s->failed;
-        s->cv_done.notify_all();
-      }
+      // the request's launches go out from a task of its own; the slot's
+      // completion event is recorded after them, and the retirement above
+      // reads it only once the task has finished
+      const int dev = s->device;
+      cudaStream_t sk = s->slots[k];
+      int* hstat = s->host_status + k;
+      cudaEvent_t done_ev = s->slot_done[k];
+      s->slot_enqueuing[k] = 1;
+      s->slot_enq[k] = std::async(std::launch::async, [prob, dev, sk, hstat, dstat, done_ev]() -> mes_status {
+        cudaSetDevice(dev);
+        mes_status st = problem_enqueue(prob, sk);
+        if (st == MES_OK && (cudaMemcpyAsync(hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, sk) != cudaSuccess ||
+                             cudaEventRecord(done_ev, sk) != cudaSuccess)) {
+          cudaGetLastError();
+          st = MES_ERR_CUDA;
+        }
+        if (st != MES_OK) cudaStreamSynchronize(sk);   // let what was enqueued finish
+        return st;
+      });
       progressed = true;
     }
     bool running = false;
@@ -436,6 +454,8 @@ extern "C" mes_status mes_serve_create(size_t hbm_budget_bytes, int max_slots, m
     return mes::fail(MES_ERR_OOM, "mes_serve_create: status words could not be allocated");
   }
   for (int k = 0; k < max_slots; ++k) s->host_status[k] = MES_OK;
+  s->slot_enq.resize(max_slots);
+  s->slot_enqueuing.assign(max_slots, 0);
   s->worker = std::thread(serve_loop, s);
   *out = s;
   return MES_OK;
