@@ -60,7 +60,7 @@ struct Pow043 {
 
 struct Pow043Smem {
   float t2[256];
-  float2 icpc[16];               // (1 / c, c^0.43) per sub-interval
+  float4 cp[16];                 // (c, 1 / c, c^0.43, 0) per sub-interval: one 16-byte load
 };
 
 // x >= 0 (zero, subnormals and a negative zero give 0)
@@ -70,11 +70,10 @@ __device__ __forceinline__ float pow043(float x, const Pow043Smem& T, const floa
   if (eb == 0 || eb > 254) return 0.f;
   const int j = (int)((u >> 19) & 15u);
   const float m = __uint_as_float((u & 0x7FFFFFu) | 0x3F800000u);
-  const float c = fmaf((float)j, 1.f / 16.f, 1.f + 1.f / 32.f);   // exact
-  const float2 t = T.icpc[j];
-  const float v = (m - c) * t.x;
+  const float4 t = T.cp[j];
+  const float v = (m - t.x) * t.y;
   const float p = fmaf(v, fmaf(v, fmaf(v, fmaf(v, a[3], a[2]), a[1]), a[0]), 1.f);
-  return (t.y * T.t2[eb - 1]) * p;
+  return (t.z * T.t2[eb - 1]) * p;
 }
 
 __device__ __forceinline__ void convert_pixel(const ColourParams& P, const float* lut_lin,
@@ -138,7 +137,7 @@ colour_kernel(const uint8_t* __restrict__ rgb8, int64_t npix, int64_t K, ColourP
     lut_p[v] = p;
     lut_lin[v] = (P.space != MES_YCBCR601) ? powf(p, P.gamma) : p;
     T.t2[v] = v < 254 ? PT.t2[v] : 0.f;
-    if (v < 16) T.icpc[v] = make_float2(PT.ic[v], PT.pc[v]);
+    if (v < 16) T.cp[v] = make_float4(1.f + (v + 0.5f) / 16.f, PT.ic[v], PT.pc[v], 0.f);
   }
   const float pa[4] = {PT.a[0], PT.a[1], PT.a[2], PT.a[3]};
   __syncthreads();

@@ -446,7 +446,6 @@ chol_cluster_kernel(const float* __restrict__ Min, int r, float shift_rel, float
 // restart together.
 // --------------------------------------------------------------------------
 constexpr int kDsmMaxR = 512;
-constexpr int kDsm4MaxR = 480;
 static_assert(kChol == 256, "the diagonal-block update maps 8 warps to 32 columns");
 constexpr int LD = PB + 1;
 
@@ -464,8 +463,8 @@ __host__ __device__ inline size_t chol_dsm_smem(int r, int cl) {
   return (size_t)((rows + rp) * LD + rp + 8) * sizeof(float);
 }
 
-// CL CTAs in the cluster: 8 for r <= kDsmMaxR, 4 (half the SMs) while the
-// owned columns still fit in one CTA's shared memory (r <= kDsm4MaxR)
+// CL CTAs in the cluster (kCL; the code holds for any CL whose owned block
+// columns fit one CTA's shared memory)
 template <int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kChol, 1)
 chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
@@ -1169,24 +1168,19 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
   if (dsm_ok < 0) {
     cudaError_t e = cudaFuncSetAttribute(chol_dsm_kernel<kCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)chol_dsm_smem(kDsmMaxR, kCL));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(chol_dsm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)chol_dsm_smem(kDsm4MaxR, 4));
     dsm_ok = (e == cudaSuccess) ? 1 : 0;
     if (e != cudaSuccess && getenv("MES_DEBUG"))
       fprintf(stderr, "[mes] shared-memory cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
     cudaGetLastError();
   }
   if (r > 128 && r <= kDsmMaxR && dsm_ok == 1) {
-    // four CTAs while the owned columns fit: half the SMs of eight, measured
-    // 104 against 95 us per factorization at r = 384 but 75.3 against 74.2
-    // stacks/s with 16 stacks sharing the GPU
-    if (r <= kDsm4MaxR)
-      chol_dsm_kernel<4><<<4, kChol, chol_dsm_smem(r, 4), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip,
-                                                                 clean);
-    else
-      chol_dsm_kernel<kCL><<<kCL, kChol, chol_dsm_smem(r, kCL), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags,
-                                                                       skip, clean);
+    // eight CTAs.  Four (half the SMs, the owned columns still fit up to
+    // r = 480) were measured: 119 against 101 us per factorization in the
+    // serialised launch list at 1920x1080, 75.3 against 74.2 stacks/s with
+    // 16 stacks sharing the GPU -- a gain within the run-to-run spread, for a
+    // longer chain per decomposition, so eight stay
+    chol_dsm_kernel<kCL><<<kCL, kChol, chol_dsm_smem(r, kCL), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags,
+                                                                     skip, clean);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return MES_OK;
     if (getenv("MES_DEBUG"))

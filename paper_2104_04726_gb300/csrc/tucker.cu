@@ -200,7 +200,10 @@ struct Driver {
       t.lower = true;
       t.skip = skipf;
       t.wait_ns = wait_ns;
-      t.fill = fill;
+      // four times the concurrency share: un-split, a few CTAs stream all of
+      // K (145 us for K = 7680 on six CTAs); four splits take about the same
+      // SM time at a quarter of the latency, on the decomposition's chain
+      t.fill = fill > 0 ? 4 * fill : 0;
       if (mes::tc_eligible(t, 3)) {
         if (!parts_ready) MES_TRY(mes::split_bf16x3(A, gparts, s * r, s * r, skipf, st));
         return mes::gemm_tc(t, 3, split_ws, split_elems, flags, st);
