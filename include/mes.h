@@ -26,6 +26,31 @@
  *    (cudaMallocAsync on `stream`) and released on the same stream before
  *    the call returns.  MES_ERR_OOM reports a failed allocation.
  *  - Invalid arguments are rejected before anything is enqueued.
+ *
+ * Environment variables read by the library
+ * -----------------------------------------
+ *  - MES_TRACE=<file>: mes_tucker_als, mes_reconstruct, mes_colour_convert
+ *    and mes_quantize_core time their phases (setup, layout, init, sweep k,
+ *    core, orthonormalise, canonical, fit for the decomposition) with CUDA
+ *    events on their stream and append one JSON line per call to <file>:
+ *    {"call": name, "phases": [[phase, ms], ...], "total_ms": ms}.  A traced
+ *    call synchronises its stream before it returns; a call made while its
+ *    stream is being captured is not timed.  Every phase is also an NVTX
+ *    range (named like the phase, nested in a range named like the call)
+ *    whether MES_TRACE is set or not; NVTX costs nothing without a tool.
+ *  - MES_FAULT: host-side fault injection for tests of the failure paths (a
+ *    comma-separated list): "alloc:<k>" makes internal allocation k of each
+ *    call fail with MES_ERR_OOM; "admit" makes the serving loop refuse every
+ *    admission (the ticket's status is MES_ERR_OOM).  Nothing touches the GPU.
+ *  - MES_TUNE=1: the first use of a tensor-core product shape times every
+ *    tile width (128, 256) and split-K factor (1..16) on the caller's stream
+ *    and keeps the fastest for the process (never under stream capture);
+ *    MES_TUNE_CACHE=<file> loads and appends the choices.  Off by default.
+ *  - MES_TC_VARIANT=p1|p2: the TF32 and BF16 products run on the persistent
+ *    tensor-core kernel (p1: one CTA per SM; p2: 128-wide tiles, two CTAs per
+ *    SM) instead of one tile per CTA.  Same results up to split-K rounding
+ *    order; a measurement switch, off by default.
+ *  - MES_DEBUG: diagnostic messages on stderr.
  */
 #ifndef MES_H
 #define MES_H

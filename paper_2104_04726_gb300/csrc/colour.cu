@@ -459,6 +459,8 @@ extern "C" mes_status mes_colour_convert(const uint8_t* rgb8, int64_t s1, int64_
     return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_convert: unknown colour space %d", space);
   if (!(gamma > 0.f)) return mes::fail(MES_ERR_INVALID_ARG, "mes_colour_convert: gamma must be > 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::Trace trace("mes_colour_convert", st);
+  trace.phase("colour");
   mes::Scratch scratch(st);
   double* partials = nullptr;
   if (norm2) MES_TRY(scratch.alloc(&partials, mes::colour_grid(s1 * s2, K)));

@@ -101,6 +101,31 @@ struct ProfScope {
   }
 };
 
+// Phase tracing of one ABI call.  Every phase is an NVTX range (free when no
+// tool is attached; ncu can filter kernels by it).  With MES_TRACE=<file> the
+// phases are also timed with CUDA events on the call's stream, and the call
+// appends one JSON line {"call", "phases": [[name, ms], ...], "total_ms"} to
+// <file> when it returns, so a traced call waits for its stream.  A call made
+// under stream capture is not timed (its NVTX ranges remain).
+class Trace {
+ public:
+  Trace(const char* call, cudaStream_t st);   // call == nullptr: inactive
+  ~Trace();
+  // ends the open phase and opens `name` (with `index` >= 0 appended)
+  void phase(const char* name, int index = -1);
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+
+ private:
+  struct Mark;
+  const char* call_;
+  char path_[512] = "";
+  cudaStream_t st_;
+  bool timed_ = false, open_ = false;
+  Mark* marks_ = nullptr;
+  int n_ = 0, cap_ = 0;
+};
+
 struct AuditScope {
   AuditScope() { audit_clear(); }
   ~AuditScope() { audit_clear(); }

@@ -274,169 +274,6 @@ chol_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __rest
 }
 
 // --------------------------------------------------------------------------
-// chol_packed: the factorization for 128 < r <= 256 on one CTA with the whole
-// lower triangle resident in shared memory (no cluster barriers, no panel
-// exchange through L2).  Packed column-major: column j holds rows
-// (j & ~3) .. rp-1 (rp = r rounded up to 32; rows and columns at and beyond
-// r are the identity), so every column starts on a 16-byte boundary and
-// the trailing update reads four rows with one 16-byte load.  Per 32-column
-// block: warp 0 factors the diagonal block in registers (warp_chol32), one
-// thread per row solves the panel (panel_step), every thread updates 4 x 4
-// tiles of the trailing lower triangle.  The same equilibration, shift and
-// restart rule as the other factorizations.
-// --------------------------------------------------------------------------
-constexpr int kPkThreads = 512;
-constexpr int kPkMaxR = 256;
-
-// start of packed column j (multiple of 4): sum over j' < j of rp - (j' & ~3)
-__host__ __device__ __forceinline__ int pk_start(int j, int rp) {
-  const int q = j >> 2, s = j & 3;
-  return 4 * q * rp - 8 * q * (q - 1) + s * (rp - 4 * q);
-}
-
-__host__ __device__ inline size_t chol_packed_smem(int r) {
-  const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
-  return ((size_t)pk_start(rp, rp) + rp /*dinv*/ + rp /*start*/ + PB * (PB + 1) /*Dg*/ +
-          (size_t)nb * PB * (PB + 1) /*inverse scratch*/) * sizeof(float);
-}
-
-__global__ void __launch_bounds__(kPkThreads, 1)
-chol_packed_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __restrict__ Lout,
-                   float* __restrict__ dinv_out, float* __restrict__ Linv_blk, int* __restrict__ flags,
-                   const int* __restrict__ skip, int* __restrict__ clean) {
-  if (skip && *skip) {
-    if (clean && threadIdx.x == 0) *clean = 1;
-    return;
-  }
-  const int rp = (r + PB - 1) / PB * PB, nb = rp / PB;
-  extern __shared__ __align__(16) float smem[];
-  float* Pk = smem;                                        // packed lower triangle
-  int* start = reinterpret_cast<int*>(Pk + pk_start(rp, rp));
-  float* dinv = reinterpret_cast<float*>(start + rp);
-  float* Dg = dinv + rp;                                   // 32 x 33
-  float* inv_scr = Dg + PB * (PB + 1);                     // nb x 32 x 33
-  __shared__ int bad;
-  __shared__ float Drc[PB];
-  __shared__ __align__(16) float colbuf[PB * PB];
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = kPkThreads / 32;
-  auto at = [&](int i, int j) -> float& { return Pk[start[j] + i - (j & ~3)]; };
-  if (t == 0 && flags) atomicAdd(flags + 1, 1);
-  for (int j = t; j < rp; j += kPkThreads) {
-    start[j] = pk_start(j, rp);
-    float dv = 0.f;
-    if (j < r) {
-      const float v = Min[j + (int64_t)r * j];
-      const bool ok = v > 0.f && isfinite(v);
-      if (!ok && flags) atomicOr(flags, 2);
-      dv = 1.f / (ok ? sqrtf(v) : 1.f);
-      dinv_out[j] = dv;
-    }
-    dinv[j] = dv;
-  }
-  __syncthreads();
-  float rel = shift_rel;
-  int restarts = 0;
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    const float shift = rel * (float)r;
-    const float floor = fmaxf(1e-7f, 0.1f * shift);
-    if (t == 0) bad = 0;
-    // A = D^-1 M D^-1 + shift I (lower part), identity beyond r
-    for (int j = warp; j < rp; j += nw) {
-      const float dj = dinv[j];
-      for (int i = (j & ~3) + lane; i < rp; i += 32) {
-        float v = 0.f;
-        if (i >= j) {
-          if (i < r && j < r) {
-            v = Min[i + (int64_t)r * j] * dinv[i] * dj;
-            if (i == j) v += shift;
-          } else if (i == j) {
-            v = 1.f;
-          }
-        }
-        at(i, j) = v;
-      }
-    }
-    __syncthreads();
-    for (int k = 0; k < nb; ++k) {
-      const int p0 = k * PB;
-      const int b = max(0, min(PB, r - p0));
-      if (warp == 0) {
-        for (int c = 0; c < PB; ++c) Dg[lane * (PB + 1) + c] = (c <= lane) ? at(p0 + lane, p0 + c) : 0.f;
-        __syncwarp();
-        warp_chol32(Dg, b, floor, &bad, colbuf, Drc);
-        __syncwarp();
-        for (int c = 0; c < PB; ++c)
-          if (c <= lane) at(p0 + lane, p0 + c) = Dg[lane * (PB + 1) + c];
-      }
-      __syncthreads();
-      const int rows = rp - p0 - PB;
-      // panel: rows below the block solve x L_kk^T = a
-      for (int ii = t; ii < rows; ii += kPkThreads) {
-        const int i = p0 + PB + ii;
-        float a[PB];
-#pragma unroll
-        for (int c = 0; c < PB; ++c) a[c] = at(i, p0 + c);
-        panel_step<0>(a, colbuf, Drc);
-#pragma unroll
-        for (int c = 0; c < PB; ++c) at(i, p0 + c) = a[c];
-      }
-      __syncthreads();
-      // trailing lower triangle: 4 x 4 tiles, row tile bi >= column tile bj
-      const int nt = rows / 4;
-      const int ntiles = nt * (nt + 1) / 2;
-      for (int tile = t; tile < ntiles; tile += kPkThreads) {
-        int bi = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
-        while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-        while (bi * (bi + 1) / 2 > tile) --bi;
-        const int bj = tile - bi * (bi + 1) / 2;
-        const int i0 = p0 + PB + 4 * bi, j0 = p0 + PB + 4 * bj;
-        float acc[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-#pragma unroll 8
-        for (int c = 0; c < PB; ++c) {
-          const float4 u = *reinterpret_cast<const float4*>(&at(i0, p0 + c));
-          const float4 v = *reinterpret_cast<const float4*>(&at(j0, p0 + c));
-          const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(uu[x], vv[y], acc[x][y]);
-        }
-#pragma unroll
-        for (int y = 0; y < 4; ++y)
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-            if (i0 + x >= j0 + y) at(i0 + x, j0 + y) -= acc[x][y];
-      }
-      __syncthreads();
-    }
-    if (!bad) break;
-    if (t == 0 && flags) {
-      atomicOr(flags, 1);
-      atomicAdd(flags + 2, 1);
-    }
-    ++restarts;
-    rel = (rel == 0.f) ? 1e-6f : rel * 10.f;
-    if (rel > 1e-2f) rel = 1e-2f;
-    __syncthreads();
-  }
-  if (clean && t == 0) *clean = restarts == 0;
-  // L (lower part of the r x r result) and the inverses of its diagonal blocks
-  for (int j = warp; j < r; j += nw)
-    for (int i = j + lane; i < r; i += 32) Lout[i + (int64_t)r * j] = at(i, j);
-  for (int k = warp; k < nb; k += nw) {
-    float* Ls = inv_scr + (size_t)k * PB * (PB + 1);
-    const int p0 = k * PB;
-    for (int c = 0; c < PB; ++c) Ls[lane * (PB + 1) + c] = (c <= lane) ? at(p0 + lane, p0 + c) : 0.f;
-    __syncwarp();
-    warp_tri_inv32(Ls, Linv_blk + (size_t)k * PB * PB);
-  }
-}
-
-// --------------------------------------------------------------------------
 // chol_cluster: the same factorization spread over a cluster of kCL CTAs on
 // kCL SMs (for r > 128, where one SM would need ~r^3/3 FP32 FMAs alone).
 // Every CTA factors the 32 x 32 diagonal block itself (same data, same code,
@@ -743,15 +580,30 @@ chol_dsm_kernel(const float* __restrict__ Min, int r, float shift_rel, float* __
     for (int k = rank, off = 0; k < nb; off += rp - PB * k, k += CL) {
       const int h = rp - PB * k;
       float* Sk = store + off * LD;
-      for (int e = t; e < h * PB; e += kChol) {
-        const int i = e % h, c = e / h;
-        const int g = PB * k + i, j = PB * k + c;
-        float v = 0.f;
-        if (g < r && j < r && g >= j) {
-          v = Min[g + (int64_t)r * j] * dinv[g] * dinv[j];
-          if (g == j) v += shift;
+      // eight loads in flight a thread before the stores (one at a time made
+      // this a chain of h / 8 round trips to L2 or DRAM)
+      for (int e0 = t; e0 < h * PB; e0 += 8 * kChol) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kChol;
+          const int i = e % h, c = e / h;
+          const int g = PB * k + i, j = PB * k + c;
+          v[u] = (e < h * PB && g < r && j < r && g >= j) ? Min[g + (int64_t)r * j] : 0.f;
         }
-        Sk[i * LD + c] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kChol;
+          if (e >= h * PB) break;
+          const int i = e % h, c = e / h;
+          const int g = PB * k + i, j = PB * k + c;
+          float a = 0.f;
+          if (g < r && j < r && g >= j) {
+            a = v[u] * dinv[g] * dinv[j];
+            if (g == j) a += shift;
+          }
+          Sk[i * LD + c] = a;
+        }
       }
     }
     __syncthreads();
@@ -1336,25 +1188,16 @@ mes_status chol(const float* M, int r, float shift_rel, float* L, float* dinv, f
       fprintf(stderr, "[mes] shared-memory cluster Cholesky disabled: %s\n", cudaGetErrorString(e));
     cudaGetLastError();
   }
-  static int pk_ok = -1;
-  if (pk_ok < 0) {
-    cudaError_t e = cudaFuncSetAttribute(chol_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)chol_packed_smem(kPkMaxR));
-    pk_ok = (e == cudaSuccess) ? 1 : 0;
-    cudaGetLastError();
-  }
-  if (r > 128 && r <= kPkMaxR && pk_ok == 1) {
-    chol_packed_kernel<<<1, kPkThreads, chol_packed_smem(r), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags, skip,
-                                                                    clean);
-    MES_LAUNCH_CHECK();
-    return MES_OK;
-  }
   if (r > 128 && r <= kDsmMaxR && dsm_ok == 1) {
     // eight CTAs.  Four (half the SMs, the owned columns still fit up to
     // r = 480) were measured: 119 against 101 us per factorization in the
     // serialised launch list at 1920x1080, 75.3 against 74.2 stacks/s with
     // 16 stacks sharing the GPU -- a gain within the run-to-run spread, for a
-    // longer chain per decomposition, so eight stay
+    // longer chain per decomposition, so eight stay.  One CTA with the packed
+    // lower triangle resident in its shared memory (r <= 256, no cluster
+    // barrier) was measured too: 107 against 74 us at r = 256, the same
+    // 75.1 stacks/s -- one SM issues too few instructions per cycle for the
+    // trailing updates
     chol_dsm_kernel<kCL><<<kCL, kChol, chol_dsm_smem(r, kCL), st>>>(M, r, shift_rel, L, dinv, Linv_blk, flags,
                                                                      skip, clean);
     cudaError_t e = cudaGetLastError();

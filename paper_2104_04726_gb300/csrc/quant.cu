@@ -146,6 +146,8 @@ extern "C" mes_status mes_quantize_core(const float* core, int N, const int64_t*
   int64_t plane_size = 0, planes = 0;
   MES_TRY(mes::quant_plane_shape(N, ranks, 65535, &plane_size, &planes, "mes_quantize_core"));   // grid.y limit
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::Trace trace("mes_quantize_core", st);
+  trace.phase("quantize");
   mes::Scratch scratch(st);
   unsigned* maxbits = nullptr;
   MES_TRY(scratch.alloc(&maxbits, (size_t)planes));

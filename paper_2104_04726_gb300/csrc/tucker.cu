@@ -462,6 +462,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   if (o.concurrency < 0) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: concurrency must be >= 0");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::Trace trace(ws_bytes ? nullptr : "mes_tucker_als", st);
   mes::AuditScope audit_scope;
   if (!ws_bytes) {
     int64_t nX = 1, nQ = 1;
@@ -589,6 +590,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   float* U1 = factors[1];
 
   // ---- second layout of T and ||T||^2 ----
+  trace.phase("layout");
   MES_TRY(mes::slice_transpose(X, s1, s2, L, XB, xpart, nblk, st, Xr, tf32, X16, XB16));
   const float* Xop = tf32 ? Xr : X;    // T as an operand of the large products
   MES_TRY(mes::sum_doubles(xpart, nblk, normX, nullptr, st));
@@ -667,6 +669,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
     return d.big(g);
   };
   // ---- initialisation: truncated or interlaced HOSVD (Eq. 6, Eq. 7) or given factors ----
+  trace.phase("init");
   if (o.init_factors) {
     for (int n = 0; n < N; ++n) {
       if (!o.init_factors[n]) return mes::fail(MES_ERR_INVALID_ARG, "mes_tucker_als: init_factors[%d] null", n);
@@ -768,6 +771,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   // ---- sweeps (Eq. 8), n = 1..N ----
   d.skip = done;
   for (int sweep = 1; sweep <= max_iters; ++sweep) {
+    trace.phase("sweep", sweep);
     // mode 1: P = T x_2 S2^T, per l: P[x][q2 + r2 l] = sum_y XB[y + s2 x + s1 s2 l] U1[y + s2 q2]
     {
       Gemm g = base();
@@ -863,6 +867,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   }
   d.skip = nullptr;
 
+  trace.phase("core");
   // ---- BF16 form: B and the core from T itself (TF32-rounded), so the
   // returned core carries no BF16 rounding of T ----
   if (bf) {
@@ -890,6 +895,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   d.fill = 0;
 
   // ---- one more CholeskyQR pass on each large factor ----
+  trace.phase("orthonormalise");
   // The sweeps orthonormalise with one pass (enough for the iteration); the
   // returned factors get a second one, S <- S R^-1, and the core follows
   // exactly: Q x_n S^T = (Q x_n R^-T) for the new S, i.e. Q <- Q x_n R^-T.
@@ -905,6 +911,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   }
 
   // ---- canonical basis of the large modes ----
+  trace.phase("canonical");
   if (canonical) {
     const int64_t ncore = r1 * r2 * Lr;
     for (int n = 0; n < 2; ++n) {
@@ -1009,6 +1016,7 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
   }
 
   // ---- fit from the explicit residual (and T_hat when asked for) ----
+  trace.phase("fit");
   if (fit || o.reconstruction) {
     const float* fac[8];
     for (int n = 0; n < N; ++n) fac[n] = factors[n];
@@ -1039,6 +1047,8 @@ extern "C" mes_status mes_reconstruct(const float* core, const float* const* fac
   if (precision != MES_PREC_FP32 && precision != MES_PREC_BF16 && precision != MES_PREC_TF32)
     return mes::fail(MES_ERR_INVALID_ARG, "mes_reconstruct: unknown precision %d", precision);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mes::Trace trace("mes_reconstruct", st);
+  trace.phase("reconstruct");
   mes::AuditScope audit_scope;
   {
     int64_t nX = 1, nQ = 1;

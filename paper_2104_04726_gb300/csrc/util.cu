@@ -5,6 +5,10 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace mes {
@@ -135,6 +139,94 @@ void prof_end(const char* family, cudaStream_t st, double flops, double bytes) {
   }
   g_recs.push_back(ProfRec{fam, g_pending, b, flops, bytes});
   g_pending = nullptr;
+}
+
+// ---- phase tracing ----
+struct Trace::Mark {
+  char name[40];
+  cudaEvent_t ev;
+};
+
+Trace::Trace(const char* call, cudaStream_t st) : call_(call), st_(st) {
+  if (!call) return;   // inactive (e.g. a workspace-size query)
+  nvtxRangePushA(call);
+  const char* path = getenv("MES_TRACE");
+  if (!path || !*path) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  if (snprintf(path_, sizeof(path_), "%s", path) >= (int)sizeof(path_)) return;
+  timed_ = true;
+  phase("setup");
+}
+
+void Trace::phase(const char* name, int index) {
+  if (!call_) return;
+  if (open_) nvtxRangePop();
+  char label[40];
+  if (index >= 0)
+    snprintf(label, sizeof(label), "%s %d", name, index);
+  else
+    snprintf(label, sizeof(label), "%s", name);
+  nvtxRangePushA(label);
+  open_ = true;
+  if (!timed_) return;
+  if (n_ == cap_) {
+    const int cap = cap_ ? 2 * cap_ : 32;
+    Mark* m = new Mark[cap];
+    for (int i = 0; i < n_; ++i) m[i] = marks_[i];
+    delete[] marks_;
+    marks_ = m;
+    cap_ = cap;
+  }
+  Mark& mk = marks_[n_];
+  snprintf(mk.name, sizeof(mk.name), "%s", label);
+  if (cudaEventCreate(&mk.ev) != cudaSuccess || cudaEventRecord(mk.ev, st_) != cudaSuccess) {
+    cudaGetLastError();
+    timed_ = false;   // tracing gives up quietly; the call itself goes on
+    return;
+  }
+  ++n_;
+}
+
+Trace::~Trace() {
+  if (!call_) return;
+  if (open_) nvtxRangePop();
+  nvtxRangePop();
+  if (!marks_) return;
+  cudaEvent_t end = nullptr;
+  bool ok = timed_ && n_ > 0 && cudaEventCreate(&end) == cudaSuccess && cudaEventRecord(end, st_) == cudaSuccess &&
+            cudaEventSynchronize(end) == cudaSuccess;
+  std::string line = std::string("{\"call\": \"") + call_ + "\", \"phases\": [";
+  float total = 0.f;
+  for (int i = 0; ok && i < n_; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, marks_[i].ev, i + 1 < n_ ? marks_[i + 1].ev : end) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    total += ms;
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%s[\"%s\", %.4f]", i ? ", " : "", marks_[i].name, ms);
+    line += buf;
+  }
+  if (ok) {
+    char buf[64];
+    snprintf(buf, sizeof(buf), "], \"total_ms\": %.4f}\n", total);
+    line += buf;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (FILE* f = fopen(path_, "a")) {
+      fputs(line.c_str(), f);
+      fclose(f);
+    }
+  }
+  cudaGetLastError();
+  for (int i = 0; i < n_; ++i) cudaEventDestroy(marks_[i].ev);
+  if (end) cudaEventDestroy(end);
+  delete[] marks_;
 }
 
 }  // namespace mes

@@ -128,3 +128,28 @@ def test_batch_problem_status(mes, scene):
     assert int(good.status.cpu()) == 0 and np.isfinite(float(good.fit))
     assert int(bad.status.cpu()) == MES_ERR_TIMEOUT and np.isnan(float(bad.fit))
 
+
+
+def test_phase_trace(mes, scene, tmp_path, monkeypatch):
+    """MES_TRACE=<file>: one JSON line per traced call with its phases timed
+    on the call's stream; a call without the variable writes nothing."""
+    import json
+    X, dims, ranks = scene
+    path = tmp_path / "trace.jsonl"
+    monkeypatch.setenv("MES_TRACE", str(path))
+    res = mes.tucker_als(X, dims, ranks, max_iters=3, tol=0.0)
+    assert int(res["status"].cpu()) == 0
+    monkeypatch.delenv("MES_TRACE")
+    mes.tucker_als(X, dims, ranks, max_iters=3, tol=0.0)
+    torch.cuda.synchronize()
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["call"] == "mes_tucker_als"
+    names = [p[0] for p in rec["phases"]]
+    assert names[:3] == ["setup", "layout", "init"]
+    assert [n for n in names if n.startswith("sweep")] == ["sweep 1", "sweep 2", "sweep 3"]
+    assert names[-1] == "fit" and "orthonormalise" in names
+    ms = [p[1] for p in rec["phases"]]
+    assert all(m >= 0.0 for m in ms) and abs(sum(ms) - rec["total_ms"]) < 1e-2 * max(1.0, rec["total_ms"])
+    assert rec["total_ms"] > 0.0
