@@ -500,6 +500,24 @@ mes_status mes_profile_get(int i, char* name, int name_len, int64_t* launches, d
 mes_status mes_gemm_selftest(int impl, const float* A, const float* B, float* C, int64_t M, int64_t N,
                              int64_t K, int batch, void* stream);
 
+/*
+ * Test hook for the factorization and solve of one CholeskyQR pass (the
+ * factor update after Eq. 8 runs them on every r x r Gram; used by the test
+ * suite to check the kernels in isolation).  H: r x r symmetric positive
+ * definite, column-major (only the lower part is read); W, V: s x r
+ * column-major; all FP32 device arrays, 1 <= r <= 1024.  Computes
+ * dinv = diag(H)^-1/2, L lower triangular with L L^T = D^-1 H D^-1
+ * (D = diag(dinv)^-1; only the lower part of L is written), and
+ * V = W D^-1 L^-T, i.e. V R = W for the upper triangular R = (D L)^T with
+ * R^T R = H.  The factorization raises a diagonal shift and restarts when a
+ * pivot falls below its floor; *restarts (nullable host int) receives the
+ * number of restarts.  Synchronises the stream.  MES_ERR_INVALID_ARG for bad
+ * sizes or W == V; MES_ERR_NONFINITE when diag(H) has a non-positive or
+ * non-finite entry.
+ */
+mes_status mes_solve_selftest(const float* H, int r, const float* W, int64_t s, float* L, float* dinv,
+                              float* V, int* restarts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

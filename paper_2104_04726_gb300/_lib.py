@@ -41,6 +41,7 @@ SIGNATURES = {
     "mes_dequantize_core": (_c.c_int, [_p, _p, _c.c_int, _i64p, _p, _p]),
     "mes_quantize_core_noalloc": (_c.c_int, [_p, _c.c_int, _i64p, _c.c_int, _p, _p, _p]),
     "mes_gemm_selftest": (_c.c_int, [_c.c_int, _p, _p, _p, _c.c_int64, _c.c_int64, _c.c_int64, _c.c_int, _p]),
+    "mes_solve_selftest": (_c.c_int, [_p, _c.c_int, _p, _c.c_int64, _p, _p, _p, _p, _p]),
     "mes_batch_create": (_c.c_int, [_c.c_int, _c.POINTER(_p)]),
     "mes_batch_run": (_c.c_int, [_p, _p, _c.c_int, _c.POINTER(_c.c_int), _p]),
     "mes_batch_capture": (_c.c_int, [_p, _p, _c.c_int, _p]),
