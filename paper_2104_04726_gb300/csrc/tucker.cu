@@ -31,6 +31,9 @@
 // 1 - sqrt(||T||^2 - ||Q||^2)/||T|| is compared with the previous one; a
 // device flag set when |change| < tol turns every later sweep's kernels into
 // no-ops, so the host enqueues max_iters sweeps without reading anything back.
+// With tol = 0 (a fixed number of sweeps), no fit history asked for and every
+// small mode at full rank, the per-sweep core and fit serve nothing and are
+// formed in the last sweep only.
 // The returned fit is recomputed from the explicit residual ||T - T_hat||,
 // which does not suffer the cancellation of ||T||^2 - ||Q||^2 in FP32.
 #include <cstdio>
@@ -850,15 +853,20 @@ static mes_status tucker_als_impl(const float* X, int N, const int64_t* dims, co
       for (int it = 0; it < inner_iters; ++it)
         MES_TRY(d.subspace_step(gz, gw, J, s2, r2, U1, Ur[1], false, nullptr, nullptr, U16[1]));
     }
-    MES_TRY(b_product());
-    // small modes n = 3..N with r_n < s_n: Gram of B x_{m != n} S_m^T, exact
-    // eigenvectors.  A full-rank small mode's factor is orthogonal: it leaves
-    // every other mode's Gram and the core norm unchanged, so its
-    // eigenvectors are taken once, after the last sweep.
-    for (int n = 2; n < N; ++n)
-      if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n, false));
-    // core Q = B x_{n>=3} S_n^T (Eq. 5 / Eq. 7 with the current factors)
-    {
+    // B, the small modes and the core of this sweep.  With every small mode
+    // at full rank nothing in the next sweep reads them: they serve the
+    // stopping test and the fit history only, so with tol = 0 (a fixed sweep
+    // count) and no history asked for they are formed in the last sweep
+    // alone (the results are the same bit for bit)
+    if (tol > 0.0 || o.fit_history || !sh.small_full || sweep == max_iters) {
+      MES_TRY(b_product());
+      // small modes n = 3..N with r_n < s_n: Gram of B x_{m != n} S_m^T, exact
+      // eigenvectors.  A full-rank small mode's factor is orthogonal: it leaves
+      // every other mode's Gram and the core norm unchanged, so its
+      // eigenvectors are taken once, after the last sweep.
+      for (int n = 2; n < N; ++n)
+        if (sh.r[n] < sh.s[n]) MES_TRY(small_mode_update(n, false));
+      // core Q = B x_{n>=3} S_n^T (Eq. 5 / Eq. 7 with the current factors)
       MES_TRY(core_from_B(done));
       MES_TRY(mes::sumsq(core, r1 * r2 * Lr, qpart, nblk, done, st));
       MES_TRY(mes::sum_doubles(qpart, nblk, normQ, done, st));
