@@ -346,6 +346,26 @@ def test_deterministic(mes):
     assert float(a["fit"].cpu()) == float(b["fit"].cpu())
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fixed_sweeps_without_history_are_the_same(mes, prec):
+    """With tol = 0, no history and full-rank small modes the per-sweep core
+    and fit are formed in the last sweep only: nothing else reads them, so
+    the result must equal, bit for bit, the run that forms them every sweep
+    (asked for by the history)."""
+    cfg, img = _scene("small_64x48")
+    T = colour.colour_convert(img, cfg["space"])
+    X = to_torch(T)
+    a = mes.tucker_als(X, T.shape, cfg["ranks"], max_iters=5, tol=0.0, precision=prec, history=False)
+    b = mes.tucker_als(X, T.shape, cfg["ranks"], max_iters=5, tol=0.0, precision=prec, history=True)
+    torch.cuda.synchronize()
+    assert int(a["iters"].cpu()) == 5 and int(b["iters"].cpu()) == 5
+    assert torch.equal(a["core"], b["core"])
+    assert all(torch.equal(x, y) for x, y in zip(a["factors"], b["factors"]))
+    assert float(a["fit"].cpu()) == float(b["fit"].cpu())
+    h = b["fit_history"].cpu().numpy()
+    assert np.isfinite(h).all() and np.all(np.diff(h) > -1e-6)
+
+
 def test_warm_start_from_oracle_factors(mes):
     cfg, img = _scene("small_64x48")
     T = colour.colour_convert(img, cfg["space"])
