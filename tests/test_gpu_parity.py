@@ -253,6 +253,24 @@ def test_ragged_shape_truncated_small_modes(mes):
             assert sin_max < 1e-3, (n, gap, sin_max)
 
 
+def test_bf16_on_unaligned_rows_runs_the_tf32_form(mes):
+    """BF16 rows must start on 16-byte boundaries for TMA, so image modes
+    that are not multiples of 8 take the TF32 form: the same decomposition
+    as asking for TF32, bit for bit, and within the TF32 tolerance of the
+    oracle."""
+    spec = synth.SceneSpec(100, 75, (0.5, 2.0), views=2, d_max=4)
+    img = synth.make_stack(spec, 33)
+    T = colour.colour_convert(img, "ipt")           # 100 x 75 x 3 x 4
+    ranks = (24, 18, 3, 4)
+    a = _run(mes, T, ranks, 10, 0.0, precision="bf16")
+    b = _run(mes, T, ranks, 10, 0.0, precision="tf32")
+    assert torch.equal(a["core"], b["core"])
+    assert all(torch.equal(x, y) for x, y in zip(a["factors"], b["factors"]))
+    ref = tucker.hooi(T, ranks, 10, 0.0)
+    fit = float(a["fit"].cpu())
+    assert abs(fit - ref.fit) / ref.fit < 1e-4, (fit, ref.fit)
+
+
 def test_mid_ranks_not_multiple_of_32(mes):
     # ranks 150 and 140 (> 128, not multiples of the 32-column blocks of the
     # cluster Cholesky and the blocked triangular solve) on a 400 x 300 scene

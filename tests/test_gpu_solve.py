@@ -68,7 +68,7 @@ def _run(lib, H, W):
 
 
 CASES = [(1, 5), (33, 100), (128, 1000), (129, 64), (200, 777), (256, 11520), (384, 7680), (385, 500),
-         (700, 300)]
+         (512, 2048), (513, 96), (700, 300)]
 
 
 @pytest.mark.parametrize("r,s", CASES)
